@@ -1,0 +1,220 @@
+/*
+ * vmat.h - C ABI of the B300 column-generation VMAT optimiser.
+ *
+ * The library solves the treatment-plan model of Men, Romeijn, Jia and Jiang
+ * ("Ultra-fast treatment plan optimization for volumetric modulated arc
+ * therapy"), Sec. 2.1, Eq. 3:
+ *
+ *     min_{y, A_k}  sum_j F(z_j) + gamma * G(y)
+ *     s.t.  z_j = sum_k y_k sum_{i in A_k} D_ij,   y_k >= 0,
+ *
+ * with the one-sided quadratic voxel cost F of Eq. 1 and the dose-rate
+ * smoothing G of Eq. 2, by column generation (Sec. 2.2): a pricing step picks
+ * the most promising deliverable aperture among beams that have none yet, and
+ * a master problem re-optimises the intensities y by gradient projection.
+ *
+ * Conventions
+ *  - Beams k = 0..N-1 are sorted by angle theta_k (degrees, strictly
+ *    increasing in [0, 360)).  Each beam has an MLC of R leaf rows x C
+ *    columns; beamlet i = (k*R + r)*C + c.  Voxel j indexes the caller's grid.
+ *  - An aperture is one open interval [l, r) of columns per leaf row
+ *    (0 <= l <= r <= C; l == r is a closed row).
+ *  - "_dev" pointers are CUDA device pointers owned by the caller (for
+ *    instance torch tensors); the library never frees them.  "_host"
+ *    pointers are ordinary host memory owned by the caller.
+ *  - Every call is enqueued on the context's stream and is synchronous on
+ *    return (the stream is synchronised before returning) unless stated.
+ *  - Every call returns a vmat_status; nothing is thrown across the ABI.
+ *    On failure vmat_last_error() gives a message.  A context is not
+ *    thread-safe: use one context per host thread.
+ *  - Device waits inside the library's kernels are bounded: a wait that runs
+ *    out returns VMAT_ETIMEOUT instead of hanging.
+ */
+#ifndef VMAT_H
+#define VMAT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VMAT_API __attribute__((visibility("default")))
+#else
+#define VMAT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VMAT_OK = 0,
+  VMAT_EINVAL = 1,   /* bad argument: sizes, unsorted CSR, non-finite value, bad state for the call */
+  VMAT_ENOMEM = 2,   /* device allocation failed */
+  VMAT_ECUDA = 3,    /* a CUDA runtime call failed */
+  VMAT_ENOTCONV = 4, /* master problem hit max_iters before the KKT tolerance (results still written) */
+  VMAT_ETIMEOUT = 5, /* a bounded device wait ran out */
+  VMAT_ESTATE = 6    /* no feasible aperture / no free beam left */
+} vmat_status;
+
+/* Storage type of D on the device.  F16/BF16 store each beamlet's row scaled
+ * by s_i = max_j D_ij (FP32 scale kept per beamlet) and accumulate in FP32. */
+typedef enum { VMAT_F64 = 0, VMAT_F32 = 1, VMAT_F16 = 2, VMAT_BF16 = 3 } vmat_dtype;
+
+typedef struct vmat_ctx vmat_ctx;
+
+/* The planning problem (Sec. 2.1).  All pointers are host memory, read
+ * during vmat_create only. */
+typedef struct {
+  int32_t n_vox;               /* |V|, voxels of the grid */
+  int32_t n_angles;            /* N */
+  int32_t n_rows, n_cols;      /* R, C: MLC leaf rows and beamlet columns */
+  const double *theta_deg;     /* [N] beam angles, strictly increasing in [0, 360) */
+  const uint8_t *struct_id;    /* [n_vox] structure of each voxel, < n_struct */
+  int32_t n_struct;            /* entries of T/alpha/beta (<= 256) */
+  const double *T;             /* [n_struct] threshold / prescription T_j (Eq. 1) */
+  const double *alpha;         /* [n_struct] underdose weight alpha_j >= 0 (Eq. 1) */
+  const double *beta;          /* [n_struct] overdose weight beta_j >= 0 (Eq. 1) */
+  double gamma;                /* smoothing weight gamma >= 0 (Eq. 3) */
+  int32_t cyclic;              /* 1: G and leaf limits run round the ring of beams; 0: path of Eq. 2 */
+  int32_t max_leaf_step;       /* leaf travel limit s: columns per angle step (>= C: unconstrained) */
+  int64_t nnz;                 /* non-zeros of D */
+  const int64_t *row_ptr;      /* [B+1] beamlet-major CSR of D, B = N*R*C */
+  const int32_t *vox_idx;      /* [nnz] voxel of each entry, strictly ascending within a row */
+  vmat_dtype val_dtype;        /* VMAT_F64 or VMAT_F32: type of val */
+  const void *val;             /* [nnz] D_ij, finite and > 0 */
+} vmat_problem;
+
+/* Size information of a context. */
+typedef struct {
+  int32_t n_vox, n_active;     /* grid voxels; voxels with at least one entry of D */
+  int32_t n_angles, n_rows, n_cols;
+  int64_t n_beamlets, nnz;
+  int32_t n_columns;           /* apertures in the current plan */
+  int64_t device_bytes;        /* device memory held by the context */
+  vmat_dtype d_dtype;
+  int32_t master_grid, master_block; /* launch shape of the master kernel */
+} vmat_info;
+
+/* Copy the problem to the device and build every storage form of D:
+ * beamlet-major CSR and a voxel-major transpose (rows sorted by beamlet),
+ * both over the compacted set of voxels D touches, in d_dtype (VMAT_F32,
+ * VMAT_F16 or VMAT_BF16).  cuda_stream: a cudaStream_t (NULL: the legacy
+ * default stream) on which every later call is enqueued.  Validates the
+ * problem (sizes, sorted rows, finite positive values, sorted angles) and
+ * returns VMAT_EINVAL on any violation.  *out is NULL on failure. */
+VMAT_API vmat_status vmat_create(const vmat_problem *prob, vmat_dtype d_dtype, void *cuda_stream,
+                        vmat_ctx **out);
+VMAT_API void vmat_destroy(vmat_ctx *ctx);
+/* Last error message of ctx (ctx NULL: of the last failed vmat_create).
+ * Valid until the next call on that context. */
+VMAT_API const char *vmat_last_error(const vmat_ctx *ctx);
+VMAT_API vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out);
+
+/* Dose of a beamlet fluence (Sec. 2.1): z_j = sum_i D_ij x_i for all grid
+ * voxels, with the voxel cost of Eq. 1.  x_dev [B] float; z_dev [n_vox]
+ * float or NULL; fprime_dev [n_vox] float F'(z_j) or NULL; cost_host: sum_j
+ * F(z_j) reduced in FP64, or NULL. */
+VMAT_API vmat_status vmat_dose(vmat_ctx *ctx, const float *x_dev, float *z_dev, float *fprime_dev,
+                      double *cost_host);
+
+/* Beamlet prices (Sec. 2.2: the KKT conditions give each beamlet the price
+ * dF/dx_i): g_i = sum_j D_ij f_j for every beamlet of a beam with
+ * angle_mask_dev[k] != 0 (angle_mask_dev NULL: all beams).  f_dev [n_vox]
+ * float (typically F'(z)); g_dev [B] float; entries of masked-out beams are
+ * not written. */
+VMAT_API vmat_status vmat_price(vmat_ctx *ctx, const float *f_dev, const uint8_t *angle_mask_dev,
+                       float *g_dev);
+
+/* One aperture: beam and leaf pair per row. */
+typedef struct {
+  int32_t angle;     /* beam index k */
+  double price;      /* total price of the aperture (sum of its row values) */
+  double runner_up;  /* least price of any other free beam (INFINITY if none) */
+  int16_t *l, *r;    /* [n_rows] host arrays, caller-allocated */
+} vmat_column;
+
+/* Pricing subproblem (Sec. 2.2): for every beam without an aperture, the
+ * deliverable aperture of least total price under the leaf-travel limits to
+ * the nearest beams with apertures, found by one left-to-right pass per leaf
+ * row; returns the beam of least price (ties: lowest index).  g_dev [B]
+ * float prices.  Row values and their prefix sums are formed in FP32 in
+ * column order; the aperture price sums the rows in FP64 in row order.
+ * VMAT_ESTATE if no beam is free or a row has no feasible interval. */
+VMAT_API vmat_status vmat_pricing_select(vmat_ctx *ctx, const float *g_dev, vmat_column *out);
+
+/* Add an aperture to the plan: builds its column of the aperture-dose matrix
+ * M[:, k] = sum_{i in A_k} D_i,: , marks the beam occupied and records its
+ * leaves; y_k starts at 0.  The leaves must satisfy 0 <= l <= r <= C (the
+ * leaf-travel limits are not re-checked: replay of a recorded plan is
+ * allowed).  VMAT_EINVAL if the beam already has an aperture. */
+VMAT_API vmat_status vmat_add_column(vmat_ctx *ctx, const vmat_column *col);
+
+/* Master problem (Sec. 2.2): minimise Eq. 3 over y >= 0 with the current
+ * apertures fixed, y_k = 0 for beams without one, by projected gradient
+ * (second Barzilai-Borwein step, exact line search on [0,1]).  Stops when
+ * rho = max_k |min(y_k, df/dy_k)| <= kkt_tol * max(rho_start, rho_ref) or
+ * after max_iters iterations (VMAT_ENOTCONV; y is still written).  y_host
+ * [N] in: warm start (NULL: keep the context's y), out: solution (NULL: not
+ * copied).  cost/kkt/iters (each may be NULL): final objective (FP64), final
+ * rho, iterations used. */
+VMAT_API vmat_status vmat_master_step(vmat_ctx *ctx, int32_t max_iters, double kkt_tol, double rho_ref,
+                             double *y_host, double *cost, double *kkt, int32_t *iters);
+
+/* Current plan dose z = sum_k y_k M[:, k] on the grid: z_dev [n_vox] float. */
+VMAT_API vmat_status vmat_plan_dose(vmat_ctx *ctx, float *z_dev);
+
+/* Clear the plan (apertures, y, dose) so a new column generation can start
+ * on the same D. */
+VMAT_API vmat_status vmat_reset(vmat_ctx *ctx);
+
+typedef struct {
+  int32_t n_iters;             /* column-generation iterations (<= N) */
+  int32_t master_max_iters;    /* per master problem */
+  double kkt_tol;              /* relative KKT tolerance of each master problem */
+  const int32_t *forced_angle; /* NULL, or [n_iters] beams to take instead of the pricing result (replay) */
+  const int16_t *forced_l;     /* [n_iters*R] leaves of the forced apertures */
+  const int16_t *forced_r;
+} vmat_colgen_opts;
+
+typedef struct {              /* caller-allocated host arrays (any may be NULL) */
+  int32_t *angle_order;       /* [n_iters] beam added at each iteration */
+  int16_t *l, *r;             /* [N*R] final leaves (rows of beams without an aperture: 0) */
+  double *y;                  /* [N] final intensities */
+  double *price;              /* [n_iters] price of the chosen aperture (pricing result) */
+  double *runner_up;          /* [n_iters] least price of the other free beams */
+  double *cost;               /* [n_iters] objective after each master problem */
+  double *kkt;                /* [n_iters] final rho of each master problem */
+  int32_t *master_iters;      /* [n_iters] */
+} vmat_colgen_result;
+
+/* Column generation (Sec. 2.2, Fig. 1) from the context's current plan:
+ * n_iters times {prices of the free beams from F'(z); pricing; add column;
+ * master problem}.  The master problems stop at kkt_tol relative to
+ * max(rho_start, rho of the plan's first master problem).  The whole loop
+ * runs on the device; the host reads the records once at the end.
+ * VMAT_ENOTCONV if some master problem hit its limit (records still
+ * written). */
+VMAT_API vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *opts,
+                            vmat_colgen_result *res);
+
+/* Batched dose of 32 fluence vectors (the differentiable forward):
+ * Z[j][b] = sum_i D_ij X[i][b], X_dev [B][32] float row-major, Z_dev
+ * [n_vox][32] float; cost_host [32] (or NULL): sum_j F(Z[j][b]) in FP64;
+ * fprime_dev [n_vox][32] float F'(Z) or NULL. */
+VMAT_API vmat_status vmat_dose_batch32(vmat_ctx *ctx, const float *X_dev, float *Z_dev, float *fprime_dev,
+                              double *cost_host);
+
+/* Batched adjoint: G[i][b] = sum_j D_ij Fp[j][b] for all beamlets, Fp_dev
+ * [n_vox][32] float, G_dev [B][32] float. */
+VMAT_API vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, float *G_dev);
+
+/* Self-test of the bounded device waits (no counterpart in the method):
+ * launches the master kernel's grid barrier with every CTA but one waiting
+ * for a CTA that never arrives, each wait limited to wait_seconds.  Returns
+ * VMAT_ETIMEOUT when the waits ran out as designed (the context stays
+ * usable), VMAT_OK if skip_one == 0 and the barrier completed normally. */
+VMAT_API vmat_status vmat_selftest_grid_wait(vmat_ctx *ctx, int32_t skip_one, double wait_seconds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMAT_H */

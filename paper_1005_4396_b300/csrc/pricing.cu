@@ -1,0 +1,297 @@
+// Pricing subproblem (Sec. 2.2) and aperture columns.
+//
+// k_pricing: one CTA per beam without an aperture.  Thread 0 finds the
+// nearest beams with apertures on each side (ring or path order); each leaf
+// row gets limits l in [Llo, Lhi], r in [Rlo, Rhi] (a leaf may move at most
+// s columns per angle step from the neighbour's), then ONE left-to-right
+// pass over its C beamlets: P[0] = 0, P[c+1] = P[c] + g_c in FP32; for each
+// r the best left leaf is the feasible l of largest P[l] (ties: largest l);
+// the row keeps the least P[r] - P[l], then the shortest interval, then the
+// smallest l.  The aperture price sums the row values in FP64, row order.
+// A row is tiny (C <= 128) and its sequential order fixes ties exactly, so
+// the scan stays sequential per thread; all rows of a beam run in parallel.
+// k_select: least aperture price over free beams (ties: lowest beam), and
+// the least price of the others.
+// k_aperture: M[:, slot] = sum over open beamlets of the chosen aperture of
+// D_i,: , by one thread per voxel over its voxel-major row (sorted by
+// beamlet, so the beam's entries are one contiguous run found by bisection).
+#include <math.h>
+
+#include "vmat_internal.cuh"
+
+__global__ void __launch_bounds__(128) k_pricing(const float *__restrict__ g,
+                                                 const uint8_t *__restrict__ occ,
+                                                 const int16_t *__restrict__ lleaf,
+                                                 const int16_t *__restrict__ rleaf, int N, int R,
+                                                 int C, int s, int cyclic, double *ap_price,
+                                                 int16_t *ap_l, int16_t *ap_r) {
+  const int k = blockIdx.x;
+  __shared__ int nb[2], dist[2];
+  __shared__ float rowv[VMAT_MAX_ROWS];
+  __shared__ int rowok[VMAT_MAX_ROWS];
+  if (occ[k]) {
+    if (threadIdx.x == 0) ap_price[k] = INFINITY;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int side = 0; side < 2; ++side) {
+      nb[side] = -1;
+      dist[side] = 0;
+      const int step = side == 0 ? -1 : 1;
+      for (int d = 1; d < N; ++d) {
+        int q = k + step * d;
+        if (cyclic) q = ((q % N) + N) % N;
+        else if (q < 0 || q >= N) break;
+        if (occ[q]) {
+          nb[side] = q;
+          dist[side] = d;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int row = threadIdx.x; row < R; row += blockDim.x) {
+    int llo = 0, lhi = C, rlo = 0, rhi = C;
+    for (int side = 0; side < 2; ++side) {
+      if (nb[side] < 0) continue;
+      const int m = s * dist[side];
+      const int ln = lleaf[nb[side] * R + row], rn = rleaf[nb[side] * R + row];
+      llo = max(llo, ln - m);
+      lhi = min(lhi, ln + m);
+      rlo = max(rlo, rn - m);
+      rhi = min(rhi, rn + m);
+    }
+    const float *gr = g + ((int64_t)k * R + row) * C;
+    float P = 0.f, Pbest = 0.f, bv = 0.f;
+    int lbest = -1, bl = 0, br = 0, found = 0;
+    for (int c = 0; c <= C; ++c) {
+      if (c > 0) P = __fadd_rn(P, gr[c - 1]);
+      if (c >= llo && c <= lhi && (lbest < 0 || P >= Pbest)) {
+        Pbest = P;
+        lbest = c;
+      }
+      if (c >= rlo && c <= rhi && lbest >= 0) {
+        const float v = __fsub_rn(P, Pbest);
+        const int len = c - lbest;
+        if (!found || v < bv || (v == bv && len < br - bl)) {
+          bv = v;
+          bl = lbest;
+          br = c;
+          found = 1;
+        }
+      }
+    }
+    rowv[row] = bv;
+    rowok[row] = found;
+    ap_l[k * R + row] = (int16_t)bl;
+    ap_r[k * R + row] = (int16_t)br;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double p = 0.0;
+    int ok = 1;
+    for (int row = 0; row < R; ++row) {
+      ok &= rowok[row];
+      p += (double)rowv[row];
+    }
+    ap_price[k] = ok ? p : NAN;
+  }
+}
+
+// Writes the selection; when rec_* are given, also the per-iteration record.
+__global__ void __launch_bounds__(256) k_select(const double *__restrict__ ap_price,
+                                                const uint8_t *__restrict__ occ,
+                                                const int16_t *__restrict__ ap_l,
+                                                const int16_t *__restrict__ ap_r, int N, int R,
+                                                SelRec *sel, int16_t *sel_l, int16_t *sel_r,
+                                                int32_t *rec_k, double *rec_p, double *rec_p2) {
+  __shared__ double sp[256];
+  __shared__ int sk[256], sbad[256];
+  __shared__ int kbest;
+  const int t = threadIdx.x;
+  double bp = INFINITY;
+  int bk = -1, bad = 0;
+  for (int k = t; k < N; k += blockDim.x) {
+    if (occ[k]) continue;
+    double p = ap_price[k];
+    if (isnan(p)) { bad = 1; continue; }
+    if (bk < 0 || p < bp) { bp = p; bk = k; }  // k ascending per thread: ties keep the lower
+  }
+  sp[t] = bp; sk[t] = bk; sbad[t] = bad;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (t < o) {
+      double p2 = sp[t + o];
+      int k2 = sk[t + o];
+      if (k2 >= 0 && (sk[t] < 0 || p2 < sp[t] || (p2 == sp[t] && k2 < sk[t]))) {
+        sp[t] = p2;
+        sk[t] = k2;
+      }
+      sbad[t] |= sbad[t + o];
+    }
+    __syncthreads();
+  }
+  if (t == 0) kbest = sk[0];
+  const int anybad = sbad[0];
+  __syncthreads();
+  const int kb = kbest;
+  // least price among the other free beams
+  double q = INFINITY;
+  for (int k = t; k < N; k += blockDim.x) {
+    if (occ[k] || k == kb) continue;
+    double p = ap_price[k];
+    if (!isnan(p) && p < q) q = p;
+  }
+  __syncthreads();
+  sp[t] = q;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (t < o) sp[t] = fmin(sp[t], sp[t + o]);
+    __syncthreads();
+  }
+  if (t == 0) {
+    SelRec r;
+    r.k = kb;
+    r.status = (kb < 0 || anybad) ? (int)VMAT_ESTATE : 0;
+    r.p = kb >= 0 ? ap_price[kb] : INFINITY;
+    r.p2 = sp[0];
+    *sel = r;
+    if (rec_k) *rec_k = kb;
+    if (rec_p) *rec_p = r.p;
+    if (rec_p2) *rec_p2 = r.p2;
+  }
+  if (kb >= 0)
+    for (int row = t; row < R; row += blockDim.x) {
+      sel_l[row] = ap_l[kb * R + row];
+      sel_r[row] = ap_r[kb * R + row];
+    }
+}
+
+vmat_status vmat_launch_pricing_rec(vmat_ctx *ctx, const float *g, int32_t *rec_k, double *rec_p,
+                                    double *rec_p2) {
+  k_pricing<<<ctx->N, 64, 0, ctx->stream>>>(g, ctx->occ, ctx->lleaf, ctx->rleaf, ctx->N, ctx->R,
+                                            ctx->C, ctx->step, ctx->cyclic, ctx->ap_price,
+                                            ctx->ap_l, ctx->ap_r);
+  k_select<<<1, 256, 0, ctx->stream>>>(ctx->ap_price, ctx->occ, ctx->ap_l, ctx->ap_r, ctx->N,
+                                       ctx->R, ctx->sel, ctx->sel_l, ctx->sel_r, rec_k, rec_p,
+                                       rec_p2);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+vmat_status vmat_launch_pricing(vmat_ctx *ctx, const float *g) {
+  return vmat_launch_pricing_rec(ctx, g, nullptr, nullptr, nullptr);
+}
+
+// replace the selection by a forced aperture (replay)
+__global__ void k_force(const int32_t *fk, const int16_t *fl, const int16_t *fr, int t, int R,
+                        SelRec *sel, int16_t *sel_l, int16_t *sel_r) {
+  if (threadIdx.x == 0) {
+    sel->k = fk[t];
+    sel->status = 0;
+  }
+  for (int row = threadIdx.x; row < R; row += blockDim.x) {
+    sel_l[row] = fl[(int64_t)t * R + row];
+    sel_r[row] = fr[(int64_t)t * R + row];
+  }
+}
+
+vmat_status vmat_launch_force(vmat_ctx *ctx, const int32_t *fk, const int16_t *fl,
+                              const int16_t *fr, int t) {
+  k_force<<<1, 128, 0, ctx->stream>>>(fk, fl, fr, t, ctx->R, ctx->sel, ctx->sel_l, ctx->sel_r);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+// ---------------------------------------------------------------- aperture column
+template <typename TV>
+__global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ ptr,
+                                                  const int32_t *__restrict__ col,
+                                                  const TV *__restrict__ val,
+                                                  const float *__restrict__ scale, int use_scale,
+                                                  int32_t Va, int32_t Vpad, int R, int C,
+                                                  const SelRec *__restrict__ sel,
+                                                  const int16_t *__restrict__ sl,
+                                                  const int16_t *__restrict__ sr,
+                                                  float *__restrict__ Mcol) {
+  __shared__ int16_t L[VMAT_MAX_ROWS], Rr[VMAT_MAX_ROWS];
+  __shared__ int sk;
+  if (threadIdx.x == 0) sk = sel->status == 0 ? sel->k : -1;
+  for (int row = threadIdx.x; row < R; row += blockDim.x) {
+    L[row] = sl[row];
+    Rr[row] = sr[row];
+  }
+  __syncthreads();
+  const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Vpad) return;
+  const int k = sk;
+  if (a >= Va || k < 0) {
+    Mcol[a] = 0.f;
+    return;
+  }
+  const int32_t RC = R * C, lo = k * RC, hi = lo + RC;
+  int64_t b = ptr[a], e = ptr[a + 1];
+  while (b < e) {  // first entry with beamlet >= lo
+    int64_t m = (b + e) >> 1;
+    if (col[m] < lo) b = m + 1;
+    else e = m;
+  }
+  const int64_t end = ptr[a + 1];
+  float acc = 0.f;
+  for (int64_t q = b; q < end; ++q) {
+    const int32_t i = col[q];
+    if (i >= hi) break;
+    const int32_t rc = i - lo, row = rc / C, c = rc - row * C;
+    if (c >= L[row] && c < Rr[row]) {
+      float v = vmat_ld(val, q);
+      acc += use_scale ? v * scale[i] : v;
+    }
+  }
+  Mcol[a] = acc;
+}
+
+// commit the selected aperture as plan column `slot`
+__global__ void k_commit(const SelRec *sel, const int16_t *sl, const int16_t *sr, int R, int slot,
+                         uint8_t *occ, int16_t *lleaf, int16_t *rleaf, int32_t *slot_beam,
+                         double *y, int *dstatus) {
+  const int k = sel->status == 0 ? sel->k : -1;
+  if (k < 0) {
+    if (threadIdx.x == 0) atomicCAS(dstatus, 0, (int)VMAT_ESTATE);
+    return;
+  }
+  for (int row = threadIdx.x; row < R; row += blockDim.x) {
+    lleaf[k * R + row] = sl[row];
+    rleaf[k * R + row] = sr[row];
+  }
+  if (threadIdx.x == 0) {
+    occ[k] = 1;
+    slot_beam[slot] = k;
+    y[k] = 0.0;
+  }
+}
+
+vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot) {
+  cudaStream_t st = ctx->stream;
+  float *Mcol = ctx->M + (size_t)slot * ctx->Vpad;
+  unsigned nb = (unsigned)((ctx->Vpad + 255) / 256);
+  int us = ctx->dt != VMAT_F32;
+#define VMAT_AP_ARGS                                                                              \
+  ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, ctx->Va, ctx->Vpad, ctx->R, \
+      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol
+  if (ctx->dt == VMAT_F32) {
+    typedef float TV;
+    k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);
+  } else if (ctx->dt == VMAT_F16) {
+    typedef __half TV;
+    k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);
+  } else {
+    typedef __nv_bfloat16 TV;
+    k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);
+  }
+#undef VMAT_AP_ARGS
+  k_commit<<<1, 128, 0, st>>>(ctx->sel, ctx->sel_l, ctx->sel_r, ctx->R, slot, ctx->occ, ctx->lleaf,
+                              ctx->rleaf, ctx->slot_beam, ctx->y, ctx->dstatus);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}

@@ -1,0 +1,384 @@
+// Sparse products with D (Sec. 2.1 dose model, Sec. 2.2 prices).
+//
+//   price  g_i = s_i * sum_j Dhat_ij f_j     beamlet-major CSR, warp per row
+//   dose   z_j = sum_i Dhat_ij (s_i x_i)     voxel-major CSR, warp per row,
+//          fused epilogue: F'(z_j) and the FP64 cost sum_j F(z_j) (Eq. 1)
+//   batched forms over 32 fluence vectors (lane = vector) for the
+//   differentiable forward and its adjoint.
+// D is streamed once per call (16-byte loads, evict-first); the dense vector
+// that is gathered (f or x, at most a few MB) stays resident in L2.
+// Dhat = D for FP32 storage; F16/BF16 store D_ij / s_i.
+#include "vmat_internal.cuh"
+
+#define WARPS_PER_BLOCK 8
+
+template <typename TV>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ float4 ld(const float *p) { return __ldcs((const float4 *)p); }
+};
+template <>
+struct Vec4<__half> {
+  static __device__ __forceinline__ float4 ld(const __half *p) {
+    uint2 u = __ldcs((const uint2 *)p);
+    __half2 a = *(__half2 *)&u.x, b = *(__half2 *)&u.y;
+    float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  }
+};
+template <>
+struct Vec4<__nv_bfloat16> {
+  static __device__ __forceinline__ float4 ld(const __nv_bfloat16 *p) {
+    uint2 u = __ldcs((const uint2 *)p);
+    __nv_bfloat162 a = *(__nv_bfloat162 *)&u.x, b = *(__nv_bfloat162 *)&u.y;
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  }
+};
+
+__device__ __forceinline__ float ld_stream(const float *p, int64_t e) { return __ldcs(p + e); }
+__device__ __forceinline__ float ld_stream(const __half *p, int64_t e) { return __half2float(p[e]); }
+__device__ __forceinline__ float ld_stream(const __nv_bfloat16 *p, int64_t e) {
+  return __bfloat162float(p[e]);
+}
+
+// sum over entries [e0, e1) of val[e] * vec[col[e]] by one warp (lane partials)
+template <typename TV>
+__device__ __forceinline__ float warp_row_dot(const int32_t *__restrict__ col,
+                                              const TV *__restrict__ val,
+                                              const float *__restrict__ vec, int64_t e0, int64_t e1,
+                                              int lane) {
+  float acc = 0.f;
+  int64_t ea = (e0 + 3) & ~(int64_t)3;
+  if (ea > e1) ea = e1;
+  if (e0 + lane < ea) acc = ld_stream(val, e0 + lane) * __ldg(vec + __ldcs(col + e0 + lane));
+  const int64_t eb = ea + ((e1 - ea) & ~(int64_t)3);
+  for (int64_t e = ea + 4 * lane; e < eb; e += 128) {
+    int4 c = __ldcs((const int4 *)(col + e));
+    float4 v = Vec4<TV>::ld(val + e);
+    acc = fmaf(v.x, __ldg(vec + c.x), acc);
+    acc = fmaf(v.y, __ldg(vec + c.y), acc);
+    acc = fmaf(v.z, __ldg(vec + c.z), acc);
+    acc = fmaf(v.w, __ldg(vec + c.w), acc);
+  }
+  if (eb + lane < e1) acc = fmaf(ld_stream(val, eb + lane), __ldg(vec + __ldcs(col + eb + lane)), acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// ---------------------------------------------------------------- price
+// mode 0: all beams; 1: beams with mask[k] != 0; 2: beams with mask[k] == 0
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price(const int64_t *__restrict__ ptr,
+                                               const int32_t *__restrict__ col,
+                                               const TV *__restrict__ val,
+                                               const float *__restrict__ scale, int use_scale,
+                                               const float *__restrict__ f,
+                                               const uint8_t *__restrict__ mask, int mode, int RC,
+                                               int64_t B, float *__restrict__ g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (i >= B) return;
+  if (mode) {
+    bool m = mask[i / RC] != 0;
+    if (m != (mode == 1)) return;
+  }
+  float acc = warp_row_dot<TV>(col, val, f, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
+  if (lane == 0) g[i] = use_scale ? acc * scale[i] : acc;
+}
+
+__global__ void k_gather_active(const float *__restrict__ full, const int32_t *__restrict__ act,
+                                int32_t Va, int32_t Vpad, float *__restrict__ out) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < Vpad) out[a] = a < Va ? full[act[a]] : 0.f;
+}
+
+vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
+                              float *g) {
+  const int64_t B = ctx->B;
+  unsigned nb = (unsigned)((B + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  const int RC = ctx->R * ctx->C;
+  int us = ctx->dt != VMAT_F32;
+  if (ctx->dt == VMAT_F32)
+    k_price<float><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
+                                                ctx->scale, us, f_act, mask, mode, RC, B, g);
+  else if (ctx->dt == VMAT_F16)
+    k_price<__half><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col,
+                                                 (const __half *)ctx->bm_val, ctx->scale, us, f_act,
+                                                 mask, mode, RC, B, g);
+  else
+    k_price<__nv_bfloat16><<<nb, 256, 0, ctx->stream>>>(
+        ctx->bm_ptr, ctx->bm_col, (const __nv_bfloat16 *)ctx->bm_val, ctx->scale, us, f_act, mask,
+        mode, RC, B, g);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act) {
+  k_gather_active<<<(ctx->Vpad + 255) / 256, 256, 0, ctx->stream>>>(full, ctx->act_vox, ctx->Va,
+                                                                    ctx->Vpad, act);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+// ---------------------------------------------------------------- dose
+template <typename TV>
+__global__ void __launch_bounds__(256) k_dose(const int64_t *__restrict__ ptr,
+                                              const int32_t *__restrict__ col,
+                                              const TV *__restrict__ val,
+                                              const float *__restrict__ x, int32_t Va,
+                                              const int32_t *__restrict__ act,
+                                              const uint8_t *__restrict__ sid,
+                                              const float *__restrict__ tabf,
+                                              const double *__restrict__ tabd,
+                                              float *__restrict__ z_full,
+                                              float *__restrict__ fp_full,
+                                              double *__restrict__ part) {
+  __shared__ double s_cost[WARPS_PER_BLOCK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t a = blockIdx.x * WARPS_PER_BLOCK + warp;
+  double c = 0.0;
+  if (a < Va) {
+    float z = warp_row_dot<TV>(col, val, x, __ldg(ptr + a), __ldg(ptr + a + 1), lane);
+    if (lane == 0) {
+      int q = sid[a];
+      int32_t j = act[a];
+      if (z_full) z_full[j] = z;
+      if (fp_full) fp_full[j] = vmat_dF(z, tabf[q], tabf[256 + q], tabf[512 + q]);
+      c = vmat_F((double)z, tabd[q], tabd[256 + q], tabd[512 + q]);
+    }
+  }
+  if (lane == 0) s_cost[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0 && part) {
+    double s = 0.0;
+    for (int q = 0; q < WARPS_PER_BLOCK; ++q) s += s_cost[q];
+    part[blockIdx.x] = s;
+  }
+}
+
+// z = 0 and F'(0) on voxels that D never reaches
+__global__ void k_fill_inactive(const int32_t *__restrict__ vox2act,
+                                const uint8_t *__restrict__ sid_full, const float *__restrict__ tabf,
+                                int32_t V, float *z_full, float *fp_full) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= V || vox2act[j] >= 0) return;
+  int q = sid_full[j];
+  if (z_full) z_full[j] = 0.f;
+  if (fp_full) fp_full[j] = vmat_dF(0.f, tabf[q], tabf[256 + q], tabf[512 + q]);
+}
+
+__global__ void k_scale_fluence(const float *__restrict__ x, const float *__restrict__ s, int64_t B,
+                                float *__restrict__ xs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) xs[i] = x[i] * s[i];
+}
+
+// fixed-order sum of n partials by one block
+__global__ void k_sum_partials(const double *__restrict__ part, int64_t n, double *out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float *fp_full,
+                             double *cost_dev) {
+  cudaStream_t st = ctx->stream;
+  const float *xin = x;
+  if (ctx->dt != VMAT_F32) {
+    k_scale_fluence<<<(unsigned)((ctx->B + 255) / 256), 256, 0, st>>>(x, ctx->scale, ctx->B, ctx->xs);
+    xin = ctx->xs;
+  }
+  unsigned nb = (unsigned)((ctx->Va + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  if (nb == 0) nb = 1;
+  if ((int64_t)nb + 1 > ctx->red_len) return vmat_fail(ctx, VMAT_EINVAL, "scratch too small");
+  double *part = cost_dev ? ctx->red : nullptr;
+#define VMAT_DOSE_ARGS                                                                        \
+  ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, xin, ctx->Va, ctx->act_vox, ctx->sid, \
+      ctx->tabf, ctx->tabd, z_full, fp_full, part
+  if (ctx->dt == VMAT_F32) {
+    typedef float TV;
+    k_dose<TV><<<nb, 256, 0, st>>>(VMAT_DOSE_ARGS);
+  } else if (ctx->dt == VMAT_F16) {
+    typedef __half TV;
+    k_dose<TV><<<nb, 256, 0, st>>>(VMAT_DOSE_ARGS);
+  } else {
+    typedef __nv_bfloat16 TV;
+    k_dose<TV><<<nb, 256, 0, st>>>(VMAT_DOSE_ARGS);
+  }
+#undef VMAT_DOSE_ARGS
+  if (z_full || fp_full)
+    k_fill_inactive<<<(ctx->V + 255) / 256, 256, 0, st>>>(ctx->vox2act, ctx->sid_full, ctx->tabf,
+                                                          ctx->V, z_full, fp_full);
+  if (cost_dev) k_sum_partials<<<1, 256, 0, st>>>(part, nb, cost_dev);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+// ---------------------------------------------------------------- batched (32 vectors)
+// Z[a][b] = sum_e Dhat[e] * X[col[e]][b]: the warp loads 32 entries of the
+// row at once and broadcasts each; lane b owns vector b.
+template <typename TV>
+__device__ __forceinline__ float warp_row_dot32(const int32_t *__restrict__ col,
+                                                const TV *__restrict__ val,
+                                                const float *__restrict__ X,
+                                                const float *__restrict__ colscale, int64_t e0,
+                                                int64_t e1, int lane) {
+  float acc = 0.f;
+  for (int64_t e = e0; e < e1; e += 32) {
+    int n = (int)min((int64_t)32, e1 - e);
+    int32_t c = 0;
+    float v = 0.f;
+    if (lane < n) {
+      c = __ldcs(col + e + lane);
+      v = ld_stream(val, e + lane);
+      if (colscale) v *= __ldg(colscale + c);
+    }
+    for (int q = 0; q < n; ++q) {
+      int32_t cq = __shfl_sync(0xffffffffu, c, q);
+      float vq = __shfl_sync(0xffffffffu, v, q);
+      acc = fmaf(vq, __ldg(X + (size_t)cq * 32 + lane), acc);
+    }
+  }
+  return acc;
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_dose32(const int64_t *__restrict__ ptr,
+                                                const int32_t *__restrict__ col,
+                                                const TV *__restrict__ val,
+                                                const float *__restrict__ scale, int use_scale,
+                                                const float *__restrict__ X, int32_t Va,
+                                                const int32_t *__restrict__ act,
+                                                const uint8_t *__restrict__ sid,
+                                                const float *__restrict__ tabf,
+                                                const double *__restrict__ tabd, float *Z,
+                                                float *Fp, double *part) {
+  __shared__ double s_cost[WARPS_PER_BLOCK][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t a = blockIdx.x * WARPS_PER_BLOCK + warp;
+  double c = 0.0;
+  if (a < Va) {
+    float z = warp_row_dot32<TV>(col, val, X, use_scale ? scale : nullptr, __ldg(ptr + a),
+                                 __ldg(ptr + a + 1), lane);
+    int q = sid[a];
+    size_t j = (size_t)act[a];
+    Z[j * 32 + lane] = z;
+    if (Fp) Fp[j * 32 + lane] = vmat_dF(z, tabf[q], tabf[256 + q], tabf[512 + q]);
+    c = vmat_F((double)z, tabd[q], tabd[256 + q], tabd[512 + q]);
+  }
+  s_cost[warp][lane] = c;
+  __syncthreads();
+  if (part && threadIdx.x < 32) {
+    double s = 0.0;
+    for (int w = 0; w < WARPS_PER_BLOCK; ++w) s += s_cost[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 32 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_fill_inactive32(const int32_t *__restrict__ vox2act,
+                                  const uint8_t *__restrict__ sid_full,
+                                  const float *__restrict__ tabf, int32_t V, float *Z, float *Fp) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)V * 32) return;
+  int32_t j = (int32_t)(t >> 5);
+  if (vox2act[j] >= 0) return;
+  int q = sid_full[j];
+  Z[t] = 0.f;
+  if (Fp) Fp[t] = vmat_dF(0.f, tabf[q], tabf[256 + q], tabf[512 + q]);
+}
+
+// per-vector fixed-order sums of nb x 32 partials
+__global__ void k_sum_partials32(const double *__restrict__ part, int64_t nb, double *out) {
+  __shared__ double sh[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int64_t q = w; q < nb; q += 8) s += part[q * 32 + lane];
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sh[q][lane];
+    out[lane] = t;
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price32(const int64_t *__restrict__ ptr,
+                                                 const int32_t *__restrict__ col,
+                                                 const TV *__restrict__ val,
+                                                 const float *__restrict__ scale, int use_scale,
+                                                 const float *__restrict__ Fa, int64_t B,
+                                                 float *__restrict__ G) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (i >= B) return;
+  float acc = warp_row_dot32<TV>(col, val, Fa, nullptr, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
+  G[(size_t)i * 32 + lane] = use_scale ? acc * scale[i] : acc;
+}
+
+__global__ void k_gather_active32(const float *__restrict__ full, const int32_t *__restrict__ act,
+                                  int32_t Va, float *__restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)Va * 32) return;
+  out[t] = full[(size_t)act[t >> 5] * 32 + (t & 31)];
+}
+
+vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, float *Fp,
+                                     double *cost_dev) {
+  cudaStream_t st = ctx->stream;
+  unsigned nb = (unsigned)((ctx->Va + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  if (nb == 0) nb = 1;
+  if ((int64_t)nb * 32 + 64 > ctx->red_len) return vmat_fail(ctx, VMAT_EINVAL, "scratch too small");
+  double *part = cost_dev ? ctx->red : nullptr;
+  int us = ctx->dt != VMAT_F32;
+#define VMAT_D32_ARGS                                                                        \
+  ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, X, ctx->Va, ctx->act_vox, \
+      ctx->sid, ctx->tabf, ctx->tabd, Z, Fp, part
+  if (ctx->dt == VMAT_F32) {
+    typedef float TV;
+    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+  } else if (ctx->dt == VMAT_F16) {
+    typedef __half TV;
+    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+  } else {
+    typedef __nv_bfloat16 TV;
+    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+  }
+#undef VMAT_D32_ARGS
+  k_fill_inactive32<<<(unsigned)(((int64_t)ctx->V * 32 + 255) / 256), 256, 0, st>>>(
+      ctx->vox2act, ctx->sid_full, ctx->tabf, ctx->V, Z, Fp);
+  if (cost_dev) k_sum_partials32<<<1, 256, 0, st>>>(part, nb, cost_dev);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}
+
+vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G) {
+  cudaStream_t st = ctx->stream;
+  if (!ctx->fa32) VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fa32, (size_t)(ctx->Va > 0 ? ctx->Va : 1) * 32));
+  float *Fa = ctx->fa32;
+  k_gather_active32<<<(unsigned)(((int64_t)ctx->Va * 32 + 255) / 256 + 1), 256, 0, st>>>(
+      Fp, ctx->act_vox, ctx->Va, Fa);
+  unsigned nb = (unsigned)((ctx->B + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  int us = ctx->dt != VMAT_F32;
+  if (ctx->dt == VMAT_F32)
+    k_price32<float><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
+                                         ctx->scale, us, Fa, ctx->B, G);
+  else if (ctx->dt == VMAT_F16)
+    k_price32<__half><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const __half *)ctx->bm_val,
+                                          ctx->scale, us, Fa, ctx->B, G);
+  else
+    k_price32<__nv_bfloat16><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col,
+                                                 (const __nv_bfloat16 *)ctx->bm_val, ctx->scale,
+                                                 us, Fa, ctx->B, G);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  return VMAT_OK;
+}

@@ -1,0 +1,355 @@
+"""Python binding of libvmat (include/vmat.h): argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels; this module passes
+torch tensors' device pointers and host numpy arrays through ctypes.  There is
+no CPU fallback: if libvmat.so is missing or no CUDA device is present,
+loading fails with an error.
+
+Module-level functions carry the C names (vmat_create, vmat_dose, ...);
+`Plan` wraps one context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvmat.so")
+
+VMAT_OK, VMAT_EINVAL, VMAT_ENOMEM, VMAT_ECUDA, VMAT_ENOTCONV, VMAT_ETIMEOUT, VMAT_ESTATE = range(7)
+VMAT_F64, VMAT_F32, VMAT_F16, VMAT_BF16 = range(4)
+DTYPES = {"f32": VMAT_F32, "f16": VMAT_F16, "bf16": VMAT_BF16}
+STATUS_NAMES = ["VMAT_OK", "VMAT_EINVAL", "VMAT_ENOMEM", "VMAT_ECUDA", "VMAT_ENOTCONV",
+                "VMAT_ETIMEOUT", "VMAT_ESTATE"]
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+class VmatError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class vmat_problem(ctypes.Structure):
+    _fields_ = [("n_vox", _i32), ("n_angles", _i32), ("n_rows", _i32), ("n_cols", _i32),
+                ("theta_deg", _p), ("struct_id", _p), ("n_struct", _i32), ("T", _p),
+                ("alpha", _p), ("beta", _p), ("gamma", _d), ("cyclic", _i32),
+                ("max_leaf_step", _i32), ("nnz", _i64), ("row_ptr", _p), ("vox_idx", _p),
+                ("val_dtype", ctypes.c_int), ("val", _p)]
+
+
+class vmat_info(ctypes.Structure):
+    _fields_ = [("n_vox", _i32), ("n_active", _i32), ("n_angles", _i32), ("n_rows", _i32),
+                ("n_cols", _i32), ("n_beamlets", _i64), ("nnz", _i64), ("n_columns", _i32),
+                ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
+                ("master_block", _i32)]
+
+
+class vmat_column(ctypes.Structure):
+    _fields_ = [("angle", _i32), ("price", _d), ("runner_up", _d), ("l", _p), ("r", _p)]
+
+
+class vmat_colgen_opts(ctypes.Structure):
+    _fields_ = [("n_iters", _i32), ("master_max_iters", _i32), ("kkt_tol", _d),
+                ("forced_angle", _p), ("forced_l", _p), ("forced_r", _p)]
+
+
+class vmat_colgen_result(ctypes.Structure):
+    _fields_ = [("angle_order", _p), ("l", _p), ("r", _p), ("y", _p), ("price", _p),
+                ("runner_up", _p), ("cost", _p), ("kkt", _p), ("master_iters", _p)]
+
+
+EXPORTS = {
+    "vmat_create": [ctypes.POINTER(vmat_problem), ctypes.c_int, _p, ctypes.POINTER(_p)],
+    "vmat_destroy": [_p],
+    "vmat_last_error": [_p],
+    "vmat_get_info": [_p, ctypes.POINTER(vmat_info)],
+    "vmat_dose": [_p, _p, _p, _p, _p],
+    "vmat_price": [_p, _p, _p, _p],
+    "vmat_pricing_select": [_p, _p, ctypes.POINTER(vmat_column)],
+    "vmat_add_column": [_p, ctypes.POINTER(vmat_column)],
+    "vmat_master_step": [_p, _i32, _d, _d, _p, _p, _p, _p],
+    "vmat_plan_dose": [_p, _p],
+    "vmat_reset": [_p],
+    "vmat_colgen_run": [_p, ctypes.POINTER(vmat_colgen_opts), ctypes.POINTER(vmat_colgen_result)],
+    "vmat_dose_batch32": [_p, _p, _p, _p, _p],
+    "vmat_price_batch32": [_p, _p, _p],
+    "vmat_selftest_grid_wait": [_p, _i32, _d],
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libvmat.so and declare its entry points (no CUDA call is made)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libvmat.so not built ({path}); run python -m paper_1005_4396_b300.build")
+        L = ctypes.CDLL(path)
+        for name, args in EXPORTS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name == "vmat_destroy" else (
+                ctypes.c_char_p if name == "vmat_last_error" else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor / host pointer of a numpy array / None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _check(ctx, status):
+    if status != VMAT_OK:
+        msg = load_library().vmat_last_error(ctx)
+        raise VmatError(status, msg.decode() if msg else "")
+
+
+def _require_cuda(t, dtype, numel, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and t.numel() == numel):
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor of {numel} elements")
+
+
+# ---------------------------------------------------------------- C-named calls
+def vmat_create(prob, dtype="f32", stream=None, val_f32=False):
+    """Create a context from an inputs.Problem; returns (ctx handle, keepalive)."""
+    L = load_library()
+    theta = np.ascontiguousarray(prob.theta_deg, dtype=np.float64)
+    sid = np.ascontiguousarray(prob.struct_id, dtype=np.uint8)
+    T = np.ascontiguousarray(prob.T, dtype=np.float64)
+    al = np.ascontiguousarray(prob.alpha, dtype=np.float64)
+    be = np.ascontiguousarray(prob.beta, dtype=np.float64)
+    rp = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
+    vx = np.ascontiguousarray(prob.vox_idx, dtype=np.int32)
+    if val_f32:
+        val = np.ascontiguousarray(prob.val, dtype=np.float32)
+        vdt = VMAT_F32
+    else:
+        val = np.ascontiguousarray(prob.val, dtype=np.float64)
+        vdt = VMAT_F64
+    cfg = prob.cfg
+    P = vmat_problem(sid.size, cfg.n_angles, cfg.n_rows, cfg.n_cols, theta.ctypes.data,
+                     sid.ctypes.data, T.size, T.ctypes.data, al.ctypes.data, be.ctypes.data,
+                     cfg.gamma, int(cfg.cyclic), int(cfg.max_leaf_step), int(rp[-1]),
+                     rp.ctypes.data, vx.ctypes.data, vdt, val.ctypes.data)
+    h = _p()
+    st = L.vmat_create(ctypes.byref(P), DTYPES[dtype], stream, ctypes.byref(h))
+    if st != VMAT_OK:
+        raise VmatError(st, L.vmat_last_error(None).decode())
+    return h
+
+
+def vmat_create_raw(P: vmat_problem, dtype=VMAT_F32, stream=None):
+    L = load_library()
+    h = _p()
+    st = L.vmat_create(ctypes.byref(P), dtype, stream, ctypes.byref(h))
+    if st != VMAT_OK:
+        raise VmatError(st, L.vmat_last_error(None).decode())
+    return h
+
+
+def vmat_destroy(ctx):
+    load_library().vmat_destroy(ctx)
+
+
+def vmat_get_info(ctx) -> dict:
+    inf = vmat_info()
+    _check(ctx, load_library().vmat_get_info(ctx, ctypes.byref(inf)))
+    return {k: getattr(inf, k) for k, _ in vmat_info._fields_}
+
+
+def vmat_dose(ctx, x, z=None, fprime=None, want_cost=True):
+    c = ctypes.c_double()
+    _check(ctx, load_library().vmat_dose(ctx, _ptr(x), _ptr(z), _ptr(fprime),
+                                         ctypes.byref(c) if want_cost else None))
+    return c.value if want_cost else None
+
+
+def vmat_price(ctx, f, g, mask=None):
+    _check(ctx, load_library().vmat_price(ctx, _ptr(f), _ptr(mask), _ptr(g)))
+
+
+def vmat_pricing_select(ctx, g, n_rows):
+    l = np.zeros(n_rows, np.int16)
+    r = np.zeros(n_rows, np.int16)
+    col = vmat_column(0, 0.0, 0.0, l.ctypes.data, r.ctypes.data)
+    _check(ctx, load_library().vmat_pricing_select(ctx, _ptr(g), ctypes.byref(col)))
+    return dict(k=col.angle, p=col.price, p2=col.runner_up, l=l, r=r)
+
+
+def vmat_add_column(ctx, k, l, r):
+    l = np.ascontiguousarray(l, dtype=np.int16)
+    r = np.ascontiguousarray(r, dtype=np.int16)
+    col = vmat_column(int(k), 0.0, 0.0, l.ctypes.data, r.ctypes.data)
+    _check(ctx, load_library().vmat_add_column(ctx, ctypes.byref(col)))
+
+
+def vmat_master_step(ctx, max_iters, kkt_tol, rho_ref=0.0, y=None):
+    """y: numpy float64 [N] warm start, updated in place (None: keep the context's y)."""
+    cost, kkt, its = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    st = load_library().vmat_master_step(ctx, int(max_iters), float(kkt_tol), float(rho_ref),
+                                         _ptr(y), ctypes.byref(cost), ctypes.byref(kkt),
+                                         ctypes.byref(its))
+    out = dict(cost=cost.value, kkt=kkt.value, iters=its.value, status=st)
+    if st not in (VMAT_OK, VMAT_ENOTCONV):
+        _check(ctx, st)
+    return out
+
+
+def vmat_plan_dose(ctx, z):
+    _check(ctx, load_library().vmat_plan_dose(ctx, _ptr(z)))
+
+
+def vmat_reset(ctx):
+    _check(ctx, load_library().vmat_reset(ctx))
+
+
+def vmat_colgen_run(ctx, N, R, n_iters, master_max_iters=100000, kkt_tol=1e-6, forced=None,
+                    allow_notconv=False):
+    fa = fl = fr = None
+    if forced is not None:
+        fa = np.ascontiguousarray(forced[0], dtype=np.int32)
+        fl = np.ascontiguousarray(forced[1], dtype=np.int16)
+        fr = np.ascontiguousarray(forced[2], dtype=np.int16)
+    opts = vmat_colgen_opts(int(n_iters), int(master_max_iters), float(kkt_tol), _ptr(fa),
+                            _ptr(fl), _ptr(fr))
+    n = max(int(n_iters), 1)
+    out = dict(k=np.zeros(n, np.int32), lleaf=np.zeros(N * R, np.int16),
+               rleaf=np.zeros(N * R, np.int16), y=np.zeros(N), p=np.zeros(n), p2=np.zeros(n),
+               cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32))
+    res = vmat_colgen_result(*[out[k].ctypes.data for k in
+                               ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters")])
+    st = load_library().vmat_colgen_run(ctx, ctypes.byref(opts), ctypes.byref(res))
+    out["status"] = st
+    if st != VMAT_OK and not (allow_notconv and st == VMAT_ENOTCONV):
+        _check(ctx, st)
+    if n_iters == 0:
+        for k in ("k", "p", "p2", "cost", "rho", "iters"):
+            out[k] = out[k][:0]
+    return out
+
+
+def vmat_dose_batch32(ctx, X, Z, fprime=None, want_cost=True):
+    c = (ctypes.c_double * 32)()
+    _check(ctx, load_library().vmat_dose_batch32(ctx, _ptr(X), _ptr(Z), _ptr(fprime),
+                                                 c if want_cost else None))
+    return np.array(c[:]) if want_cost else None
+
+
+def vmat_price_batch32(ctx, Fp, G):
+    _check(ctx, load_library().vmat_price_batch32(ctx, _ptr(Fp), _ptr(G)))
+
+
+def vmat_selftest_grid_wait(ctx, skip_one, wait_seconds):
+    """Status of the bounded-wait self-test (VMAT_ETIMEOUT expected with skip_one)."""
+    return load_library().vmat_selftest_grid_wait(ctx, int(skip_one), float(wait_seconds))
+
+
+# ---------------------------------------------------------------- convenience
+class Plan:
+    """One library context over a planning problem (inputs.Problem)."""
+
+    def __init__(self, prob, dtype="f32", val_f32=False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1005_4396_b300.vmat needs a CUDA device")
+        self.prob = prob
+        self.cfg = prob.cfg
+        self.stream = torch.cuda.current_stream()
+        self.ctx = vmat_create(prob, dtype, ctypes.c_void_p(self.stream.cuda_stream), val_f32)
+        self.info = vmat_get_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            vmat_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # tensors -------------------------------------------------------
+    def _t(self, n, dtype=None):
+        import torch
+        return torch.empty(n, dtype=dtype or torch.float32, device="cuda")
+
+    def dose(self, x):
+        import torch
+        _require_cuda(x, torch.float32, self.cfg.n_beamlets, "x")
+        z = self._t(self.prob.n_vox)
+        fp = self._t(self.prob.n_vox)
+        cost = vmat_dose(self.ctx, x, z, fp)
+        return z, fp, cost
+
+    def price(self, f, mask=None):
+        import torch
+        _require_cuda(f, torch.float32, self.prob.n_vox, "f")
+        g = torch.zeros(self.cfg.n_beamlets, dtype=torch.float32, device="cuda")
+        m = None
+        if mask is not None:
+            m = torch.as_tensor(np.asarray(mask, dtype=np.uint8), device="cuda")
+        vmat_price(self.ctx, f, g, m)
+        return g
+
+    def pricing_select(self, g):
+        import torch
+        _require_cuda(g, torch.float32, self.cfg.n_beamlets, "g")
+        return vmat_pricing_select(self.ctx, g, self.cfg.n_rows)
+
+    def add_column(self, k, l, r):
+        vmat_add_column(self.ctx, k, l, r)
+
+    def master_step(self, max_iters=100000, kkt_tol=1e-6, rho_ref=0.0, y=None):
+        return vmat_master_step(self.ctx, max_iters, kkt_tol, rho_ref, y)
+
+    def plan_dose(self):
+        z = self._t(self.prob.n_vox)
+        vmat_plan_dose(self.ctx, z)
+        return z
+
+    def reset(self):
+        vmat_reset(self.ctx)
+
+    def colgen_run(self, n_iters=None, master_max_iters=100000, kkt_tol=None, forced=None,
+                   allow_notconv=False):
+        n_iters = self.cfg.iterations if n_iters is None else n_iters
+        kkt_tol = self.cfg.kkt_eps if kkt_tol is None else kkt_tol
+        return vmat_colgen_run(self.ctx, self.cfg.n_angles, self.cfg.n_rows, n_iters,
+                               master_max_iters, kkt_tol, forced, allow_notconv)
+
+    def dose_batch32(self, X, want_fprime=True):
+        import torch
+        _require_cuda(X, torch.float32, self.cfg.n_beamlets * 32, "X")
+        Z = self._t(self.prob.n_vox * 32)
+        Fp = self._t(self.prob.n_vox * 32) if want_fprime else None
+        cost = vmat_dose_batch32(self.ctx, X, Z, Fp)
+        return Z, Fp, cost
+
+    def price_batch32(self, Fp):
+        import torch
+        _require_cuda(Fp, torch.float32, self.prob.n_vox * 32, "Fp")
+        G = self._t(self.cfg.n_beamlets * 32)
+        vmat_price_batch32(self.ctx, Fp, G)
+        return G
