@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the column-generation VMAT optimiser on one B300.
+
+A step is one whole plan: 180 column-generation iterations (prices ->
+pricing -> aperture column -> master problem) on the prostate-scale phantom
+(128x128x64 voxels at 3 mm, 180 beams, 40x40 MLC, 4.51e8 non-zeros of D, FP32
+D).  value = column-generation iterations per second over all ranks, inputs
+resident in HBM.  Also reported: the roofline of the dominant kernel, the
+sparse products' HBM bandwidth, FP16/BF16-D plans with their dose error
+against the FP64 oracle, an end-to-end figure through the C-ABI from host
+buffers, and the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torch.distributed.run, one independent plan per rank
+(replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
+UNIT = "CG iters/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = []
+        reasons = set()
+        smax = 0.0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    from paper_1005_4396_b300 import inputs
+    return {"prostate": inputs.prostate_config, "tiny": inputs.tiny_config,
+            "headneck": inputs.headneck_config}[name]()
+
+
+def _describe(cfg, prob):
+    return (f"{cfg.name}: {cfg.nx}x{cfg.ny}x{cfg.nz} voxels at {cfg.h} mm, {cfg.n_angles} beams, "
+            f"{cfg.n_rows}x{cfg.n_cols} MLC, {prob.n_beamlets} beamlets, nnz(D)={prob.nnz}, "
+            f"{cfg.iterations} CG iterations per plan, master KKT {cfg.kkt_eps:g}")
+
+
+def _algorithmic_bytes(prob, info, rec):
+    """Bytes each kernel must move per launch by its definition (not counting
+    re-reads): master: every PG iteration reads the columns twice (gradient
+    pass, direction pass) plus one read at entry and one at exit, and writes
+    z and F'; price: the D rows of the free beams (8 B/nnz FP32 value+index,
+    8 B row pointer), the prices written, F' gathered once."""
+    cfg = prob.cfg
+    RC = cfg.n_rows * cfg.n_cols
+    Va = info["n_active"]
+    vb = 8 if info["d_dtype"] == 1 else 6
+    nnz_beam = np.add.reduceat(np.diff(prob.row_ptr), np.arange(0, prob.n_beamlets, RC))
+    free_nnz = nnz_beam.sum()
+    master, price = [], []
+    for t, k in enumerate(rec["k"]):
+        ncol = t + 1
+        P = int(rec["iters"][t])
+        master.append((2 * P + 2) * ncol * Va * 4 + 8 * Va)
+        free_beams = cfg.n_angles - t
+        price.append(free_nnz * vb + free_beams * RC * (8 + 4) + 4 * Va)
+        free_nnz -= nnz_beam[k]
+    return np.array(master, dtype=np.float64), np.array(price, dtype=np.float64)
+
+
+def _dose_err(prob, plan_f, plan_ref_dose, lleaf, rleaf, y):
+    """max/mean |z - z_FP64| over voxels, in % of the largest prescription."""
+    import oracle
+    x = oracle.aperture_fluence(prob.cfg, lleaf, rleaf, y)
+    z64 = oracle.dose(prob, x)
+    d = np.abs(plan_ref_dose.astype(np.float64) - z64)
+    rx = float(prob.T.max())
+    return float(d.max() / rx * 100), float(d.mean() / rx * 100)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_1005_4396_b300 import inputs, vmat
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peak, peak_kind = _peaks()
+    cfg = _workload(args.workload)
+    prob = inputs.make_problem(cfg)
+    plan = vmat.Plan(prob, val_f32=True)
+    info = plan.info
+    plan.set_profiling(True)
+
+    kkt = max(cfg.kkt_eps, 1e-6)  # FP32 gradients: relative KKT 1e-6 is the reachable floor
+
+    def step():
+        plan.reset()
+        return plan.colgen_run(kkt_tol=kkt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = plan.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    recs = [step() for _ in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    launches = plan.launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    iters_per_plan = cfg.iterations
+    total_units = ws * args.steps * iters_per_plan
+    value = total_units / (ms / 1e3)
+
+    # per-phase device time and the roofline of the dominant kernel
+    phase = np.sum([r["phase_ms"] for r in recs], axis=0)  # [n_iter, 4]
+    ph_tot = phase.sum(axis=0) / args.steps
+    names = ["price_spmv", "pricing", "aperture", "master"]
+    mb, pb = zip(*[_algorithmic_bytes(prob, info, r) for r in recs])
+    mb = np.sum(mb, axis=0) / args.steps
+    pb = np.sum(pb, axis=0) / args.steps
+    master_gbs = mb.sum() / (ph_tot[3] / 1e3) / 1e9
+    price_gbs = pb.sum() / (ph_tot[0] / 1e3) / 1e9
+    dom = int(np.argmax(ph_tot))
+    dom_gbs = {0: price_gbs, 3: master_gbs}.get(dom)
+    n_master = len(recs[0]["k"])
+    roofline = {
+        "kernel": {0: "k_price", 1: "k_pricing", 2: "k_aperture", 3: "k_master"}[dom],
+        "bound": "hbm", "achieved": round(dom_gbs, 1) if dom_gbs else None,
+        "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4) if dom_gbs else None,
+        "peak_kind": f"{peak_kind} copy bandwidth",
+        "traffic": None,
+        "launches_per_step": n_master,
+        "note": ("master algorithmic bytes = (2*P+2) column reads of 4 B x active voxels per "
+                 "launch; the columns fit in L2 while a plan has < ~70 of them, so part of "
+                 "this traffic is served from L2"),
+    }
+    # stand-alone SpMV bandwidth of the two sparse products at full D (FP32)
+    x = torch.rand(prob.n_beamlets, device="cuda")
+    f = torch.randn(prob.n_vox, device="cuda")
+    z = torch.empty(prob.n_vox, device="cuda")
+    g = torch.empty(prob.n_beamlets, device="cuda")
+    spmv = {}
+    for name, fn, byts in [
+            ("dose", lambda: vmat.vmat_dose(plan.ctx, x, z, None, False),
+             prob.nnz * 8 + (info["n_active"] + 1) * 8 + info["n_active"] * 8 + prob.n_beamlets * 4),
+            ("price", lambda: vmat.vmat_price(plan.ctx, f, g, None),
+             prob.nnz * 8 + (prob.n_beamlets + 1) * 8 + prob.n_beamlets * 4 + info["n_active"] * 8)]:
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 20
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        t_ms = a.elapsed_time(b) / n
+        gbs = byts / (t_ms / 1e3) / 1e9
+        spmv[name] = {"ms": round(t_ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+                      "frac_nominal_8TBs": round(gbs / 8000.0, 4)}
+    spmv["note"] = ("host-timed around the C-ABI call (includes its stream synchronisation); "
+                    "bytes: 8 B/nnz (FP32 value + int32 index) + row pointers + vectors")
+    spmv["price_in_plan_GB/s"] = round(price_gbs, 1)
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded phantom and ray/Gaussian D; no clinical data)",
+           "config": {"workload": _describe(cfg, prob), "parallelism": f"replicas x{ws}",
+                      "l2": "inputs larger than L2 (D 3.6 GB per copy, aperture-dose matrix up to "
+                            f"{info['n_active'] * cfg.n_angles * 4 / 1e6:.0f} MB); no flush",
+                      "active_voxels": info["n_active"],
+                      "master_launch": [info["master_grid"], info["master_block"]]},
+           "gpu_launches": int(launches),
+           "roofline": roofline, "spmv": spmv,
+           "phases_ms_per_plan": {n: round(float(v), 3) for n, v in zip(names, ph_tot)},
+           "pg_iters_per_plan": int(np.mean([r["iters"].sum() for r in recs])),
+           "final_cost": float(recs[-1]["cost"][-1]),
+           "clocks": clocks}
+
+    if rank == 0 and ws == 1 and not args.quick:
+        out["variants"] = run_variants(prob, plan, recs[-1], kkt)
+        out["e2e"] = run_e2e(prob, args)
+        out["cpu_baseline"] = run_cpu_baseline(prob, args)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_variants(prob, plan32, rec32, kkt=1e-6):
+    """FP16-D and BF16-D plans: throughput and dose error against the FP64 oracle."""
+    import torch
+    from paper_1005_4396_b300 import vmat
+    res = {}
+    z32 = plan32.plan_dose().cpu().numpy()
+    e32 = _dose_err(prob, plan32, z32, rec32["lleaf"], rec32["rleaf"], rec32["y"])
+    res["f32"] = {"max_dose_err_pct_rx": round(e32[0], 5), "mean_dose_err_pct_rx": round(e32[1], 6)}
+    for dt in ("f16", "bf16"):
+        with vmat.Plan(prob, dtype=dt, val_f32=True) as p:
+            p.reset()
+            p.colgen_run(kkt_tol=kkt)
+            p.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r = p.colgen_run(kkt_tol=kkt)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            z = p.plan_dose().cpu().numpy()
+            emax, emean = _dose_err(prob, p, z, r["lleaf"], r["rleaf"], r["y"])
+            same = int(np.sum(r["k"] == rec32["k"]))
+            res[dt] = {"cg_iters_per_s": round(len(r["k"]) / t, 3),
+                       "max_dose_err_pct_rx": round(emax, 4), "mean_dose_err_pct_rx": round(emean, 5),
+                       "within_0.5pct": bool(emax <= 0.5),
+                       "final_cost": float(r["cost"][-1]),
+                       "beams_in_same_order_as_f32": same,
+                       "device_bytes": p.info["device_bytes"]}
+    res["note"] = ("dose error: the plan's own dose on the GPU against the FP64 oracle's dose of "
+                   "the same apertures and intensities, % of the largest prescription")
+    return res
+
+
+def run_e2e(prob, args):
+    """Same metric through the C-ABI from pinned host buffers: create (H2D of
+    D and the problem), one plan, read back the result, destroy."""
+    import torch
+    from paper_1005_4396_b300 import vmat
+    cfg = prob.cfg
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t, t.numpy()
+
+    keep = []
+    arrs = {}
+    for name, a in [("theta", prob.theta_deg.astype(np.float64)), ("sid", prob.struct_id),
+                    ("T", prob.T), ("alpha", prob.alpha), ("beta", prob.beta),
+                    ("row_ptr", prob.row_ptr), ("vox", prob.vox_idx),
+                    ("val", prob.val.astype(np.float32))]:
+        t, v = pinned(a)
+        keep.append(t)
+        arrs[name] = v
+    h2d = sum(v.nbytes for v in arrs.values())
+    P = vmat.vmat_problem(prob.n_vox, cfg.n_angles, cfg.n_rows, cfg.n_cols,
+                          arrs["theta"].ctypes.data, arrs["sid"].ctypes.data, arrs["T"].size,
+                          arrs["T"].ctypes.data, arrs["alpha"].ctypes.data, arrs["beta"].ctypes.data,
+                          cfg.gamma, int(cfg.cyclic), cfg.max_leaf_step, prob.nnz,
+                          arrs["row_ptr"].ctypes.data, arrs["vox"].ctypes.data, vmat.VMAT_F32,
+                          arrs["val"].ctypes.data)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n = cfg.iterations
+    times = []
+    d2h = 0
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = vmat.vmat_create_raw(P, vmat.VMAT_F32, stream)
+        r = vmat.vmat_colgen_run(ctx, cfg.n_angles, cfg.n_rows, n, 100000, max(cfg.kkt_eps, 1e-6))
+        vmat.vmat_destroy(ctx)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        d2h = sum(r[k].nbytes for k in ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters"))
+    t = min(times[1:]) if len(times) > 1 else times[0]
+    return {"value": round(n / t, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "s_per_plan": round(t, 3),
+            "note": "vmat_create from pinned host arrays (D copied, transposed on the device) "
+                    "+ vmat_colgen_run (180 iterations) + results to host + vmat_destroy"}
+
+
+def _oracle_sample(prob, n_iter):
+    import oracle
+    t0 = time.perf_counter()
+    rec = oracle.colgen(prob, n_iter=n_iter)
+    return time.perf_counter() - t0, rec
+
+
+def run_cpu_baseline(prob, args):
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    n = args.cpu_iters
+    dt, _ = _oracle_sample(prob, n)
+    return {"value": round(n / dt, 4), "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": f"first {n} column-generation iterations of the same plan (FP64 oracle, "
+                      f"OpenMP over {cores} threads, {dt:.1f} s); early iterations have the "
+                      f"fewest columns, so this overstates the oracle's whole-plan rate"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from paper_1005_4396_b300 import inputs
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cfg = _workload(args.workload)
+    prob = inputs.make_problem(cfg)
+    n = args.cpu_iters
+    for _ in range(args.warmup):
+        _oracle_sample(prob, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_sample(prob, n)
+    dt = time.perf_counter() - t0
+    value = args.steps * n / dt
+    sample = (f"each step: the first {n} column-generation iterations of the plan "
+              f"(FP64 oracle, {cores} threads)")
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": _describe(cfg, prob)}, "impl": "reference",
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": int(cores),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="prostate", choices=["prostate", "tiny", "headneck"])
+    ap.add_argument("--cpu-iters", type=int, default=16)
+    ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,6 +92,7 @@ typedef struct {
   int64_t device_bytes;        /* device memory held by the context */
   vmat_dtype d_dtype;
   int32_t master_grid, master_block; /* launch shape of the master kernel */
+  int64_t n_launches;          /* kernels this context has launched so far */
 } vmat_info;
 
 /* Copy the problem to the device and build every storage form of D:
@@ -184,6 +185,9 @@ typedef struct {              /* caller-allocated host arrays (any may be NULL) 
   double *cost;               /* [n_iters] objective after each master problem */
   double *kkt;                /* [n_iters] final rho of each master problem */
   int32_t *master_iters;      /* [n_iters] */
+  double *phase_ms;           /* [n_iters*4] device time (ms) of each iteration's phases:
+                                 prices, pricing, aperture column, master problem;
+                                 written only while profiling is on */
 } vmat_colgen_result;
 
 /* Column generation (Sec. 2.2, Fig. 1) from the context's current plan:
@@ -195,6 +199,11 @@ typedef struct {              /* caller-allocated host arrays (any may be NULL) 
  * written). */
 VMAT_API vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *opts,
                             vmat_colgen_result *res);
+
+/* Profiling: with on != 0, vmat_colgen_run brackets each phase of every
+ * iteration with CUDA events on the context's stream and reports the device
+ * times in vmat_colgen_result.phase_ms.  Off by default. */
+VMAT_API vmat_status vmat_set_profiling(vmat_ctx *ctx, int32_t on);
 
 /* Batched dose of 32 fluence vectors (the differentiable forward):
  * Z[j][b] = sum_i D_ij X[i][b], X_dev [B][32] float row-major, Z_dev

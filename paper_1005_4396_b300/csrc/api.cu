@@ -137,6 +137,7 @@ extern "C" vmat_status vmat_plan_dose(vmat_ctx *ctx, float *z_dev) {
     k_scatter_active<<<(ctx->Va + 255) / 256, 256, 0, ctx->stream>>>(ctx->zact, ctx->act_vox,
                                                                      ctx->Va, z_dev);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
   return sync_status(ctx);
 }
 
@@ -196,21 +197,36 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   }
   vmat_status s = VMAT_OK;
   const bool fresh = ctx->n_slots == 0;
+  // optional phase timing: 5 events per iteration bracket its 4 phases
+  const bool prof = ctx->profiling && res && res->phase_ms && n > 0;
+  std::vector<cudaEvent_t> ev;
+  if (prof) {
+    ev.resize((size_t)n * 5);
+    for (auto &e : ev) VMAT_CUDA(ctx, cudaEventCreate(&e));
+  }
+  auto mark = [&](int t, int q) {
+    if (prof) cudaEventRecord(ev[(size_t)t * 5 + q], st);
+  };
   for (int t = 0; t < n && s == VMAT_OK; ++t) {
+    mark(t, 0);
     // prices of the free beams from F'(z) of the current plan dose
     s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g);
     if (s != VMAT_OK) break;
+    mark(t, 1);
     s = vmat_launch_pricing_rec(ctx, ctx->g, rec.k + t, rec.p + t, rec.p2 + t);
     if (s != VMAT_OK) break;
     if (fk) {
       s = vmat_launch_force(ctx, fk, fl, fr, t);
       if (s != VMAT_OK) break;
     }
+    mark(t, 2);
     s = vmat_launch_add_column(ctx, ctx->n_slots);
     if (s != VMAT_OK) break;
     ctx->n_slots += 1;
+    mark(t, 3);
     s = vmat_launch_master(ctx, o->master_max_iters, o->kkt_tol, 0.0, fresh && t == 0 ? 1 : 0,
                            rec.cost + t, rec.rho + t, rec.iters + t, rec.status + t);
+    mark(t, 4);
   }
   if (fk) {  // the beam actually added at each step is the forced one
     cudaMemcpyAsync(rec.k, fk, n * 4, cudaMemcpyDeviceToDevice, st);
@@ -231,6 +247,16 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   if (res && res->y) cudaMemcpyAsync(res->y, ctx->y, (size_t)N * 8, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(blk, st);
   vmat_status s2 = sync_status(ctx);
+  if (prof) {
+    if (s == VMAT_OK && s2 == VMAT_OK)
+      for (int t = 0; t < n; ++t)
+        for (int q = 0; q < 4; ++q) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, ev[(size_t)t * 5 + q], ev[(size_t)t * 5 + q + 1]);
+          res->phase_ms[(size_t)t * 4 + q] = ms;
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+  }
   if (s != VMAT_OK) return s;
   if (s2 != VMAT_OK) return s2;
   if (res) {
@@ -270,4 +296,10 @@ extern "C" vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, fl
   vmat_status s = vmat_launch_price_batch32(ctx, Fp_dev, G_dev);
   if (s != VMAT_OK) return s;
   return sync_status(ctx);
+}
+
+extern "C" vmat_status vmat_set_profiling(vmat_ctx *ctx, int32_t on) {
+  if (!ctx) return VMAT_EINVAL;
+  ctx->profiling = on ? 1 : 0;
+  return VMAT_OK;
 }

@@ -621,6 +621,7 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   VMAT_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)ctx->master_smem));
   VMAT_CUDA(ctx, cudaLaunchCooperativeKernel(fn, grid, block, args, ctx->master_smem, ctx->stream));
+  ctx->n_launches += 1;
   return VMAT_OK;
 }
 
@@ -645,6 +646,7 @@ extern "C" vmat_status vmat_selftest_grid_wait(vmat_ctx *ctx, int32_t skip_one, 
   int grid = ctx->num_sms < 8 ? ctx->num_sms : 8;
   VMAT_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_grid_wait_probe, dim3(grid), dim3(32),
                                              args, 0, st));
+  ctx->n_launches += 1;
   int ds = 0;
   VMAT_CUDA(ctx, cudaMemcpyAsync(&ds, ctx->dstatus, 4, cudaMemcpyDeviceToHost, st));
   VMAT_CUDA(ctx, cudaStreamSynchronize(st));

@@ -177,6 +177,7 @@ vmat_status vmat_launch_pricing_rec(vmat_ctx *ctx, const float *g, int32_t *rec_
                                        ctx->R, ctx->sel, ctx->sel_l, ctx->sel_r, rec_k, rec_p,
                                        rec_p2);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 2;
   return VMAT_OK;
 }
 
@@ -201,6 +202,7 @@ vmat_status vmat_launch_force(vmat_ctx *ctx, const int32_t *fk, const int16_t *f
                               const int16_t *fr, int t) {
   k_force<<<1, 128, 0, ctx->stream>>>(fk, fl, fr, t, ctx->R, ctx->sel, ctx->sel_l, ctx->sel_r);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
   return VMAT_OK;
 }
 
@@ -293,5 +295,6 @@ vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot) {
   k_commit<<<1, 128, 0, st>>>(ctx->sel, ctx->sel_l, ctx->sel_r, ctx->R, slot, ctx->occ, ctx->lleaf,
                               ctx->rleaf, ctx->slot_beam, ctx->y, ctx->dstatus);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 2;
   return VMAT_OK;
 }

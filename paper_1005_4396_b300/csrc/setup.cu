@@ -460,6 +460,7 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
   out->d_dtype = ctx->dt;
   out->master_grid = ctx->master_grid;
   out->master_block = ctx->master_block;
+  out->n_launches = ctx->n_launches;
   return VMAT_OK;
 }
 
@@ -486,6 +487,7 @@ extern "C" vmat_status vmat_reset(vmat_ctx *ctx) {
   k_init_fprime<<<(ctx->Vpad + 255) / 256, 256, 0, st>>>(ctx->sid, ctx->tabf, ctx->Vpad, ctx->zact,
                                                           ctx->fpact);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
   VMAT_CUDA(ctx, cudaStreamSynchronize(st));
   ctx->n_slots = 0;
   return VMAT_OK;

@@ -112,6 +112,7 @@ vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *
         ctx->bm_ptr, ctx->bm_col, (const __nv_bfloat16 *)ctx->bm_val, ctx->scale, us, f_act, mask,
         mode, RC, B, g);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
   return VMAT_OK;
 }
 
@@ -119,6 +120,7 @@ vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act) {
   k_gather_active<<<(ctx->Vpad + 255) / 256, 256, 0, ctx->stream>>>(full, ctx->act_vox, ctx->Va,
                                                                     ctx->Vpad, act);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
   return VMAT_OK;
 }
 
@@ -220,6 +222,7 @@ vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float
                                                           ctx->V, z_full, fp_full);
   if (cost_dev) k_sum_partials<<<1, 256, 0, st>>>(part, nb, cost_dev);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1 + (ctx->dt != VMAT_F32) + ((z_full || fp_full) ? 1 : 0) + (cost_dev ? 1 : 0);
   return VMAT_OK;
 }
 
@@ -358,6 +361,7 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
       ctx->vox2act, ctx->sid_full, ctx->tabf, ctx->V, Z, Fp);
   if (cost_dev) k_sum_partials32<<<1, 256, 0, st>>>(part, nb, cost_dev);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 2 + (cost_dev ? 1 : 0);
   return VMAT_OK;
 }
 
@@ -380,5 +384,6 @@ vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G) 
                                                  (const __nv_bfloat16 *)ctx->bm_val, ctx->scale,
                                                  us, Fa, ctx->B, G);
   VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 2;
   return VMAT_OK;
 }

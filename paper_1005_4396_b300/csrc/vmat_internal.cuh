@@ -90,6 +90,8 @@ struct vmat_ctx {
   int master_grid = 0, master_block = 0, master_vpt = 0;
   size_t master_smem = 0;
   int64_t device_bytes = 0;
+  int64_t n_launches = 0;      // kernels launched by this context
+  int profiling = 0;
 };
 
 // ---------------------------------------------------------------- helpers

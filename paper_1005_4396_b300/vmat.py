@@ -48,7 +48,7 @@ class vmat_info(ctypes.Structure):
     _fields_ = [("n_vox", _i32), ("n_active", _i32), ("n_angles", _i32), ("n_rows", _i32),
                 ("n_cols", _i32), ("n_beamlets", _i64), ("nnz", _i64), ("n_columns", _i32),
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
-                ("master_block", _i32)]
+                ("master_block", _i32), ("n_launches", _i64)]
 
 
 class vmat_column(ctypes.Structure):
@@ -62,7 +62,8 @@ class vmat_colgen_opts(ctypes.Structure):
 
 class vmat_colgen_result(ctypes.Structure):
     _fields_ = [("angle_order", _p), ("l", _p), ("r", _p), ("y", _p), ("price", _p),
-                ("runner_up", _p), ("cost", _p), ("kkt", _p), ("master_iters", _p)]
+                ("runner_up", _p), ("cost", _p), ("kkt", _p), ("master_iters", _p),
+                ("phase_ms", _p)]
 
 
 EXPORTS = {
@@ -81,6 +82,7 @@ EXPORTS = {
     "vmat_dose_batch32": [_p, _p, _p, _p, _p],
     "vmat_price_batch32": [_p, _p, _p],
     "vmat_selftest_grid_wait": [_p, _i32, _d],
+    "vmat_set_profiling": [_p, _i32],
 }
 
 _lib = None
@@ -230,15 +232,17 @@ def vmat_colgen_run(ctx, N, R, n_iters, master_max_iters=100000, kkt_tol=1e-6, f
     n = max(int(n_iters), 1)
     out = dict(k=np.zeros(n, np.int32), lleaf=np.zeros(N * R, np.int16),
                rleaf=np.zeros(N * R, np.int16), y=np.zeros(N), p=np.zeros(n), p2=np.zeros(n),
-               cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32))
+               cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32),
+               phase_ms=np.zeros((n, 4)))
     res = vmat_colgen_result(*[out[k].ctypes.data for k in
-                               ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters")])
+                               ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters",
+                                "phase_ms")])
     st = load_library().vmat_colgen_run(ctx, ctypes.byref(opts), ctypes.byref(res))
     out["status"] = st
     if st != VMAT_OK and not (allow_notconv and st == VMAT_ENOTCONV):
         _check(ctx, st)
     if n_iters == 0:
-        for k in ("k", "p", "p2", "cost", "rho", "iters"):
+        for k in ("k", "p", "p2", "cost", "rho", "iters", "phase_ms"):
             out[k] = out[k][:0]
     return out
 
@@ -252,6 +256,10 @@ def vmat_dose_batch32(ctx, X, Z, fprime=None, want_cost=True):
 
 def vmat_price_batch32(ctx, Fp, G):
     _check(ctx, load_library().vmat_price_batch32(ctx, _ptr(Fp), _ptr(G)))
+
+
+def vmat_set_profiling(ctx, on):
+    _check(ctx, load_library().vmat_set_profiling(ctx, int(on)))
 
 
 def vmat_selftest_grid_wait(ctx, skip_one, wait_seconds):
@@ -331,6 +339,12 @@ class Plan:
 
     def reset(self):
         vmat_reset(self.ctx)
+
+    def set_profiling(self, on=True):
+        vmat_set_profiling(self.ctx, on)
+
+    def launches(self):
+        return vmat_get_info(self.ctx)["n_launches"]
 
     def colgen_run(self, n_iters=None, master_max_iters=100000, kkt_tol=None, forced=None,
                    allow_notconv=False):
