@@ -93,6 +93,10 @@ typedef struct {
   vmat_dtype d_dtype;
   int32_t master_grid, master_block; /* launch shape of the master kernel */
   int64_t n_launches;          /* kernels this context has launched so far */
+  double master_ms[4];         /* master kernel, cumulative device time (ms) in: gradient
+                                  pass + its reduction, step, direction pass, line search */
+  int64_t master_syncs;        /* cumulative grid-wide barriers of the master kernel */
+  int64_t master_pg_iters;     /* cumulative projected-gradient iterations */
 } vmat_info;
 
 /* Copy the problem to the device and build every storage form of D:

@@ -4,26 +4,37 @@
 // dose of the aperture added s-th (unit intensity), stored slot-major with
 // a padded column stride Vpad.
 //
-// One cooperative launch runs the whole solve.  Each CTA owns a fixed slice
-// of voxels; each thread keeps the dose z and the direction image w of its
-// voxels in registers for the whole solve.  Per iteration:
-//   pass A  reads M once: per-slot partial sums of M^T F'(z)        (HBM/L2)
-//           -> grid reduce in a fixed order (deterministic)
-//   every CTA then forms the same direction d = P+(y - s g) - y with the
-//   second Barzilai-Borwein step s
-//   pass B  reads M once: z = M y (refreshed exactly) and w = M d
-//   line search: phi'(t) = sum_j w_j F'(z_j + t w_j) + gamma*(dG.d + 2t G(d))
-//           is piecewise linear and nondecreasing; bracketing Newton rounds,
-//           two trial points per grid reduction, on register-resident z, w.
+// One cooperative launch runs the whole solve.  CTA b owns the voxel tile
+// [b*T, (b+1)*T), T = threads * VPT; thread t owns the float4 groups
+// 4*(t + threads*m), m < VPT/4, of the tile and keeps their dose z and
+// direction image w in registers for the whole solve.  Per iteration:
+//   pass A   gradient M^T F'(z): F' of the tile goes to shared memory; warp w
+//            takes slots w, w+W, ... and streams each slot's tile (T floats,
+//            contiguous) with many independent 16-byte loads per lane
+//   reduce   per-slot CTA partials -> grid barrier -> warp-per-slot fixed-order
+//            sums over CTAs -> grid barrier (deterministic, no float atomics)
+//   step     every CTA forms the same d = P+(y - s g) - y (second
+//            Barzilai-Borwein step s) from the same reduced gradient
+//   pass B   z = M y (refreshed exactly) and w = M d, thread per voxel
+//   search   phi'(t) = sum_j w_j F'(z_j + t w_j) + gamma*(dG(y).d + 2t G(d))
+//            is piecewise linear and nondecreasing: each round evaluates it
+//            at 16 points (FP32 per voxel, FP64 across warps and CTAs), one
+//            grid reduction per round; stop once Newton steps from both ends
+//            of the bracket agree (same linear piece: the secant is exact).
 // Stop: rho = max_k |min(y_k, g_k)| <= tol * max(rho_start, rho_ref).
-// Every grid-wide wait is bounded (time and spin count); a wait that runs
-// out sets VMAT_ETIMEOUT and all CTAs leave the kernel.
+// The grid barrier is one counter whose top bit flips when every CTA has
+// arrived; each wait is bounded in time and spins, after which the kernel
+// records VMAT_ETIMEOUT and every CTA leaves.
 #include <math.h>
 
 #include "vmat_internal.cuh"
 
-#define LS_ROUNDS 12
-#define PART_EXTRA 16  // per-CTA partial row: [N slots | 2x4 line search | cost | spare]
+#define LS_POINTS 16
+#define LS_ROUNDS 4
+// per-CTA partial row: [N slots | 2 x 32 line-search values | cost | spare]
+#define PART_EXTRA 72
+#define LS_OFF(N, parity) ((N) + 32 * (parity))
+#define COST_OFF(N) ((N) + 64)
 
 struct MasterArgs {
   const float *M;
@@ -34,14 +45,15 @@ struct MasterArgs {
   const double *tabd;
   const double *theta;
   double gamma, kkt_tol, rho_ref;
-  double *y;            // [N] in/out
-  double *rho_plan;     // [1] read (max with rho_ref) and, if set_rho_plan, written
-  double *part;         // [grid][N + PART_EXTRA]
-  double *gred;         // [N]
-  unsigned *bar;        // [2]
+  double *y;             // [N] in/out
+  double *rho_plan;      // [1] read (max with rho_ref) and, if set_rho_plan, written
+  double *part;          // [grid][N + PART_EXTRA]
+  double *gred;          // [N]
+  unsigned *bar;         // [1] grid barrier word
   int *dstatus;
   float *z_out, *fp_out;  // [Vpad]
   MasterOut *out;
+  double *stats;         // [8] cumulative: ns in pass A+reduce, step, pass B, search; syncs; iters
   double *rec_cost, *rec_rho;
   int32_t *rec_iters, *rec_status;
   double inactive_cost;
@@ -49,38 +61,36 @@ struct MasterArgs {
 };
 
 // ---------------------------------------------------------------- grid barrier
-// Sense by generation counter.  Returns false if this or another CTA failed
-// (timeout or an error raised elsewhere); the caller then leaves the kernel.
+// Every CTA adds 1 to the barrier word except CTA 0, which adds
+// 0x80000000 - (G-1): the sum over a barrier is 0x80000000, so the top bit
+// flips exactly when all have arrived and the low bits return to their
+// previous value (no reset).  Returns false if a wait ran out or another CTA
+// reported an error; the caller then leaves the kernel.
 __device__ __forceinline__ bool grid_sync(unsigned *bar, int *dstatus, unsigned long long wait_ns,
                                           int *s_ok) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = bar + 1;
-    volatile int *vst = dstatus;
+    const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    unsigned old, cur;
     int ok = 1;
-    unsigned g0 = *vgen;
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long t0 = vmat_globaltimer();
-      unsigned spins = 0;
-      while (*vgen == g0) {
-        if (*vst != 0) { ok = 0; break; }
-        if (++spins > (1u << 26) || ((spins & 63) == 0 && vmat_globaltimer() - t0 > wait_ns)) {
+    __threadfence();  // the CTA's partials (ordered by the bar.sync above) before arriving
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc)
+                 : "memory");
+    const unsigned long long t0 = vmat_globaltimer();
+    unsigned spins = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+      if ((old ^ cur) & 0x80000000u) break;
+      if ((++spins & 63) == 0) {
+        if (*(volatile int *)dstatus != 0) { ok = 0; break; }
+        if (spins > (1u << 26) || vmat_globaltimer() - t0 > wait_ns) {
           atomicCAS(dstatus, 0, (int)VMAT_ETIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    if (*vst != 0) ok = 0;
-    __threadfence();
+    if (ok && *(volatile int *)dstatus != 0) ok = 0;
     *s_ok = ok;
   }
   __syncthreads();
@@ -100,41 +110,21 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Block-wide sum of NV doubles per thread, fixed order; result valid in all threads.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double *s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Warp transpose-reduction: v[32] per lane in, lane l returns the warp sum of
+// v[l] (31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-  __syncthreads();
-  if (lane == 0)
+  for (int k = 16; k >= 1; k >>= 1) {
+    const bool upper = (lane & k) != 0;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) s_red[q * 32 + warp] = v[q];
-  __syncthreads();
-  if (warp == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double x = lane < nw ? s_red[q * 32 + lane] : 0.0;
-      s_red[q * 32 + lane] = 0.0;
-      x = warp_sum(x);
-      if (lane == 0) s_red[8 * 32 + q] = x;
+    for (int i = 0; i < k; ++i) {
+      const float send = upper ? v[i] : v[i + k];
+      const float keep = upper ? v[i + k] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
     }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = s_red[8 * 32 + q];
-  __syncthreads();
-}
-
-// Sum over CTAs of NV partials stored at part[c*stride + off + q], fixed order.
-template <int NV>
-__device__ __forceinline__ void grid_gather_sum(const double *part, int stride, int off,
-                                                double (&v)[NV], double *s_red) {
-#pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = 0.0;
-  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += __ldcg(part + (size_t)c * stride + off + q);
-  block_sum<NV>(v, s_red);
+  }
+  return v[0];
 }
 
 // derivative of the smoothing term G (Eq. 2) at beam k
@@ -154,44 +144,73 @@ __device__ __forceinline__ double dG_beam(const double *y, const double *theta, 
   return r;
 }
 
-struct LsPoint {
-  double t, f, h;
-};
+// G(u) over all pairs (Eq. 2), by one warp; valid in every lane
+__device__ __forceinline__ double G_warp(const double *u, const double *theta, int N, int cyclic) {
+  const int lane = threadIdx.x & 31;
+  double g = 0.0;
+  const int npair = cyclic ? N : N - 1;
+  for (int k = lane; k < npair; k += 32) {
+    int kp = k + 1 < N ? k + 1 : 0;
+    double gap = k + 1 < N ? theta[kp] - theta[k] : theta[0] + 360.0 - theta[N - 1];
+    double dd = u[kp] - u[k];
+    g += dd * dd / gap;
+  }
+  return warp_sum(g);
+}
 
-// phi'(t) and phi''(t+) of the line search at two trial points, one grid
-// reduction for both (partials double-buffered by round parity).
+// One line-search round: phi' and phi''(t+) at LS_POINTS points for this
+// thread's voxels (FP32), summed over the CTA (FP32 in a warp, FP64 across
+// warps), written as this CTA's partials and grid-reduced in FP64 in a fixed
+// order.  Out: s_res[0..15] = sums of phi' terms, s_res[16..31] = phi''.
 template <int VPT>
-__device__ __forceinline__ bool ls_eval2(const MasterArgs &a, const float (&z)[VPT],
+__device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[VPT],
                                          const float (&w)[VPT], const uint8_t (&sid)[VPT],
-                                         const float *s_tab, double *s_red, int *s_i,
-                                         int &parity, int stride, double gdot, double Gd,
-                                         double t1, double t2, LsPoint &p1, LsPoint &p2) {
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  const float tf1 = (float)t1, tf2 = (float)t2;
+                                         const float *s_tab, const float *s_t, float *s_ls,
+                                         double *s_res, int *s_ok, int parity, int stride) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  float v[32];
+#pragma unroll
+  for (int p = 0; p < 32; ++p) v[p] = 0.f;
 #pragma unroll
   for (int q = 0; q < VPT; ++q) {
     const float wq = w[q];
+    if (wq == 0.f) continue;
     const int id = sid[q];
     const float T = s_tab[id], al = s_tab[256 + id], be = s_tab[512 + id];
-    const float e1 = fmaf(tf1, wq, z[q]) - T;
-    const float c1 = e1 > 0.f ? be : (e1 < 0.f ? al : (wq > 0.f ? be : al));
-    const float e2 = fmaf(tf2, wq, z[q]) - T;
-    const float c2 = e2 > 0.f ? be : (e2 < 0.f ? al : (wq > 0.f ? be : al));
-    v[0] += (double)(2.f * c1 * e1 * wq);
-    v[1] += (double)(2.f * c1 * wq * wq);
-    v[2] += (double)(2.f * c2 * e2 * wq);
-    v[3] += (double)(2.f * c2 * wq * wq);
+    const float e0 = z[q] - T;
+    const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
+#pragma unroll
+    for (int p = 0; p < LS_POINTS; ++p) {
+      const float e = fmaf(s_t[p], wq, e0);
+      const float c = e > 0.f ? be : (e < 0.f ? al : cw);
+      const float cwq = 2.f * c * wq;
+      v[p] = fmaf(cwq, e, v[p]);
+      v[LS_POINTS + p] = fmaf(cwq, wq, v[LS_POINTS + p]);
+    }
   }
-  block_sum<4>(v, s_red);
-  const int N = a.N, off = N + 4 * parity;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 4; ++q) a.part[(size_t)blockIdx.x * stride + off + q] = v[q];
-  if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) return false;
-  grid_gather_sum<4>(a.part, stride, off, v, s_red);
-  parity ^= 1;
-  const double c0 = a.gamma * gdot, c1 = 2.0 * a.gamma * Gd;
-  p1.t = t1; p1.f = v[0] + c0 + c1 * t1; p1.h = v[1] + c1;
-  p2.t = t2; p2.f = v[2] + c0 + c1 * t2; p2.h = v[3] + c1;
+  const float ws = warp_transpose_sum32(v);
+  s_ls[warp * 32 + lane] = ws;
+  __syncthreads();
+  const int off = LS_OFF(a.N, parity);
+  if (warp == 0) {
+    double acc = 0.0;
+    for (int q = 0; q < nwarp; ++q) acc += (double)s_ls[q * 32 + lane];
+    a.part[(size_t)blockIdx.x * stride + off + lane] = acc;
+  }
+  if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_ok)) return false;
+  // sum the CTAs' partials: thread (warp, lane) takes CTAs warp, warp + W, ...
+  double acc = 0.0;
+  for (int c = warp; c < (int)gridDim.x; c += nwarp)
+    acc += __ldcg(a.part + (size_t)c * stride + off + lane);
+  double *s_tmp = s_res + 32;  // [nwarp][32]
+  s_tmp[warp * 32 + lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double r = 0.0;
+    for (int q = 0; q < nwarp; ++q) r += s_tmp[q * 32 + lane];
+    s_res[lane] = r;
+  }
+  __syncthreads();
   return true;
 }
 
@@ -201,21 +220,25 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   const int N = a.N, ns = a.nslots, tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   const int stride = N + PART_EXTRA;
-  constexpr int NG = VPT / 4;  // float4 groups per thread
+  constexpr int NG = VPT / 4;       // float4 groups per thread
+  const int tile = nthr * VPT;      // voxels per CTA
+  const int lane4 = tile / 128;     // float4s per lane when a warp streams a tile
 
-  double *s_y = (double *)smem;   // [N] per beam
-  double *s_d = s_y + N;          // [N] per beam
-  double *s_g = s_d + N;          // [N] per slot
-  double *s_gold = s_g + N;       // [N] per slot
-  double *s_dy = s_gold + N;      // [N] per slot
-  double *s_red = s_dy + N;       // [9*32]
-  double *s_sc = s_red + 9 * 32;  // [16] scalars shared by the CTA
-  float *s_yf = (float *)(s_sc + 16);  // [N] per slot
-  float *s_df = s_yf + N;              // [N] per slot
-  float *s_tab = s_df + N;             // [768]
-  float *s_wp = s_tab + 768;           // [nwarp][N]
-  int *s_i = (int *)(s_wp + nwarp * N);  // [8] ints: 0 ok, 1 flag, 2 beam scratch
-  int *s_beam = s_i + 8;                 // [N] beam of slot
+  double *s_y = (double *)smem;      // [N] per beam
+  double *s_d = s_y + N;             // [N] per beam
+  double *s_g = s_d + N;             // [N] per slot
+  double *s_gold = s_g + N;          // [N] per slot
+  double *s_dy = s_gold + N;         // [N] per slot
+  double *s_sc = s_dy + N;           // [32] CTA-wide scalars
+  double *s_res = s_sc + 32;         // [32 + 16*32] line-search sums and scratch
+  float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [N] per slot
+  float *s_df = s_yf + N;                         // [N] per slot
+  float *s_tab = s_df + N;                        // [768]
+  float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
+  float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
+  float *s_fp = s_ls + 16 * 32;                   // [tile] F' of the tile
+  int *s_i = (int *)(s_fp + tile);                // [8]
+  int *s_beam = s_i + 8;                          // [N] beam of slot
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
   for (int k = tid; k < N; k += nthr) {
@@ -230,8 +253,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   __syncthreads();
   for (int s = tid; s < ns; s += nthr) s_yf[s] = (float)s_y[s_beam[s]];
 
-  // own voxels: float4 group m covers voxels base + 4*(tid + nthr*m) .. +3
-  const size_t base = (size_t)blockIdx.x * nthr * VPT;
+  const size_t base = (size_t)blockIdx.x * tile;
   uint8_t my_sid[VPT];
 #pragma unroll
   for (int m = 0; m < NG; ++m)
@@ -243,12 +265,13 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   // z = M y
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
+#pragma unroll 4
   for (int s = 0; s < ns; ++s) {
     const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
     const float ys = s_yf[s];
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
-      float4 q = __ldg(Ms + tid + nthr * m);
+      const float4 q = __ldg(Ms + tid + nthr * m);
       z[4 * m] = fmaf(q.x, ys, z[4 * m]);
       z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
       z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
@@ -256,71 +279,71 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     }
   }
 
-  int it = 0, status = VMAT_ENOTCONV;
+  int it = 0, status = VMAT_ENOTCONV, nsync = 0;
   double rho = 0.0, rho0 = 0.0, tol = 0.0;
   bool alive = true;
   int ls_parity = 0;
+  unsigned long long tA = 0, tS = 0, tB = 0, tL = 0, c0 = 0;
+  const bool timer = blockIdx.x == 0 && tid == 0;
 
   for (;;) {
-    // ---------------- pass A: per-slot partials of M^T F'(z)
-    float fp[VPT];
+    if (timer) c0 = vmat_globaltimer();
+    // ---------------- pass A: per-slot CTA partials of M^T F'(z)
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      int q = my_sid[v];
-      fp[v] = vmat_dF(z[v], s_tab[q], s_tab[256 + q], s_tab[512 + q]);
-    }
-    for (int s0 = 0; s0 < ns; s0 += 4) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (s0 + u < ns) {
-          const float4 *Ms = (const float4 *)(a.M + (size_t)(s0 + u) * a.Vpad + base);
-#pragma unroll
-          for (int m = 0; m < NG; ++m) {
-            float4 q = __ldg(Ms + tid + nthr * m);
-            acc[u] = fmaf(q.x, fp[4 * m], acc[u]);
-            acc[u] = fmaf(q.y, fp[4 * m + 1], acc[u]);
-            acc[u] = fmaf(q.z, fp[4 * m + 2], acc[u]);
-            acc[u] = fmaf(q.w, fp[4 * m + 3], acc[u]);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = warp_sumf(acc[u]);
-      if (lane == 0)
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (s0 + u < ns) s_wp[warp * N + s0 + u] = acc[u];
+    for (int m = 0; m < NG; ++m) {
+      float4 f;
+      int id = my_sid[4 * m];
+      f.x = vmat_dF(z[4 * m], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      id = my_sid[4 * m + 1];
+      f.y = vmat_dF(z[4 * m + 1], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      id = my_sid[4 * m + 2];
+      f.z = vmat_dF(z[4 * m + 2], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      id = my_sid[4 * m + 3];
+      f.w = vmat_dF(z[4 * m + 3], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      *(float4 *)(s_fp + 4 * (tid + nthr * m)) = f;
     }
     __syncthreads();
-    for (int s = tid; s < ns; s += nthr) {
-      double sum = 0.0;
-      for (int q = 0; q < nwarp; ++q) sum += (double)s_wp[q * N + s];
-      a.part[(size_t)blockIdx.x * stride + s] = sum;
+    for (int s = warp; s < ns; s += nwarp) {
+      const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
+      const float4 *F4 = (const float4 *)s_fp;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int i = 0; i < lane4; ++i) {
+        const float4 q = __ldg(Ms + lane + 32 * i);
+        const float4 f = F4[lane + 32 * i];
+        acc = fmaf(q.x, f.x, acc);
+        acc = fmaf(q.y, f.y, acc);
+        acc = fmaf(q.z, f.z, acc);
+        acc = fmaf(q.w, f.w, acc);
+      }
+      acc = warp_sumf(acc);
+      if (lane == 0) a.part[(size_t)blockIdx.x * stride + s] = (double)acc;
     }
+    ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
-    // distributed fixed-order reduction: CTA b owns slots b, b+G, ...
-    for (int s = blockIdx.x; s < ns; s += gridDim.x) {
-      double v[1];
-      grid_gather_sum<1>(a.part, stride, s, v, s_red);
-      if (tid == 0) a.gred[s] = v[0];
+    // fixed-order sums over CTAs: warp w of CTA b owns slot b + G*w
+    for (int s = blockIdx.x + (int)gridDim.x * warp; s < ns; s += (int)gridDim.x * nwarp) {
+      double acc = 0.0;
+      for (int c = lane; c < (int)gridDim.x; c += 32) acc += __ldcg(a.part + (size_t)c * stride + s);
+      acc = warp_sum(acc);
+      if (lane == 0) a.gred[s] = acc;
     }
+    ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
+    if (timer) { unsigned long long c1 = vmat_globaltimer(); tA += c1 - c0; c0 = c1; }
 
     // ---------------- gradient, residual, direction (same in every CTA)
-    for (int s = tid; s < ns; s += nthr) {
-      int k = s_beam[s];
-      s_g[s] = __ldcg(a.gred + s) + a.gamma * dG_beam(s_y, a.theta, N, a.cyclic, k);
-    }
+    for (int s = tid; s < ns; s += nthr)
+      s_g[s] = __ldcg(a.gred + s) + a.gamma * dG_beam(s_y, a.theta, N, a.cyclic, s_beam[s]);
     __syncthreads();
     if (warp == 0) {
       double r = 0.0, ym = 0.0, gm = 0.0, dyg = 0.0, dgg = 0.0;
       for (int s = lane; s < ns; s += 32) {
-        double yk = s_y[s_beam[s]], gk = s_g[s];
+        const double yk = s_y[s_beam[s]], gk = s_g[s];
         r = fmax(r, fabs(fmin(yk, gk)));
         ym = fmax(ym, fabs(yk));
         gm = fmax(gm, fabs(gk));
-        double dg = gk - s_gold[s];
+        const double dg = gk - s_gold[s];
         dyg += s_dy[s] * dg;
         dgg += dg * dg;
       }
@@ -341,110 +364,118 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     rho = s_sc[0];
     if (it == 0) {
       rho0 = rho;
-      double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
+      const double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
       tol = a.kkt_tol * fmax(fmax(rho0, ref), 1e-300);
     }
     if (rho <= tol) { status = VMAT_OK; break; }
     if (it >= a.max_iters) { status = VMAT_ENOTCONV; break; }
     const double step = s_sc[1];
     for (int s = tid; s < ns; s += nthr) {
-      int k = s_beam[s];
-      double yk = s_y[k];
-      double p = yk - step * s_g[s];
-      double dk = (p > 0.0 ? p : 0.0) - yk;
+      const int k = s_beam[s];
+      const double yk = s_y[k];
+      const double p = yk - step * s_g[s];
+      const double dk = (p > 0.0 ? p : 0.0) - yk;
       s_d[k] = dk;
       s_df[s] = (float)dk;
       s_gold[s] = s_g[s];
     }
     __syncthreads();
-    // gdot = dG(y).d over beams with a column; Gd = G(d) over all pairs
-    if (warp == 0) {
-      double gd = 0.0, Gd = 0.0;
-      for (int s = lane; s < ns; s += 32) {
-        int k = s_beam[s];
-        gd += dG_beam(s_y, a.theta, N, a.cyclic, k) * s_d[k];
-      }
-      int npair = a.cyclic ? N : N - 1;
-      for (int k = lane; k < npair; k += 32) {
-        int kp = k + 1 < N ? k + 1 : 0;
-        double gap = k + 1 < N ? a.theta[kp] - a.theta[k] : a.theta[0] + 360.0 - a.theta[N - 1];
-        double dd = s_d[kp] - s_d[k];
-        Gd += dd * dd / gap;
-      }
+    if (warp == 0) {  // gdot = dG(y).d over beams with a column, Gd = G(d)
+      double gd = 0.0;
+      for (int s = lane; s < ns; s += 32)
+        gd += dG_beam(s_y, a.theta, N, a.cyclic, s_beam[s]) * s_d[s_beam[s]];
       gd = warp_sum(gd);
-      Gd = warp_sum(Gd);
+      const double Gd = G_warp(s_d, a.theta, N, a.cyclic);
       if (lane == 0) { s_sc[2] = gd; s_sc[3] = Gd; }
     }
     __syncthreads();
     const double gdot = s_sc[2], Gd = s_sc[3];
+    if (timer) { unsigned long long c1 = vmat_globaltimer(); tS += c1 - c0; c0 = c1; }
 
     // ---------------- pass B: z = M y, w = M d
 #pragma unroll
     for (int v = 0; v < VPT; ++v) { z[v] = 0.f; w[v] = 0.f; }
+#pragma unroll 4
     for (int s = 0; s < ns; ++s) {
       const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
       const float ys = s_yf[s], ds = s_df[s];
 #pragma unroll
       for (int m = 0; m < NG; ++m) {
-        float4 q = __ldg(Ms + tid + nthr * m);
-        z[4 * m] = fmaf(q.x, ys, z[4 * m]);       w[4 * m] = fmaf(q.x, ds, w[4 * m]);
+        const float4 q = __ldg(Ms + tid + nthr * m);
+        z[4 * m] = fmaf(q.x, ys, z[4 * m]);         w[4 * m] = fmaf(q.x, ds, w[4 * m]);
         z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]); w[4 * m + 1] = fmaf(q.y, ds, w[4 * m + 1]);
         z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]); w[4 * m + 2] = fmaf(q.z, ds, w[4 * m + 2]);
         z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]); w[4 * m + 3] = fmaf(q.w, ds, w[4 * m + 3]);
       }
     }
+    if (timer) { unsigned long long c1 = vmat_globaltimer(); tB += c1 - c0; c0 = c1; }
 
     // ---------------- exact line search on [0, 1]
-    LsPoint p0, p1;
-    if (!ls_eval2<VPT>(a, z, w, my_sid, s_tab, s_red, s_i, ls_parity, stride, gdot, Gd, 0.0, 1.0,
-                       p0, p1)) { alive = false; break; }
-    double t;
-    if (!(p0.f < 0.0)) {
-      t = 0.0;  // not a descent direction: stalled
-    } else if (p1.f <= 0.0) {
-      t = 1.0;
-    } else {
-      LsPoint lo = p0, hi = p1;
-      t = -1.0;
-      for (int r = 0; r < LS_ROUNDS; ++r) {
-        const double width = hi.t - lo.t;
-        const double tS = lo.t - lo.f * width / (hi.f - lo.f);
-        double tA = lo.h > 0.0 ? lo.t - lo.f / lo.h : tS;
-        double tB = hi.h > 0.0 ? hi.t - hi.f / hi.h : tS;
-        // both ends on one linear piece of phi': the secant root is exact
-        if ((fabs(tA - tB) <= 1e-9 * tS && fabs(tA - tS) <= 1e-9 * tS) || width <= 1e-9 * hi.t) {
-          t = tS;
-          break;
+    const double cg0 = a.gamma * gdot, cg1 = 2.0 * a.gamma * Gd;
+    double lo_t = 0.0, lo_f = 0.0, lo_h = 0.0, hi_t = 1.0, hi_f = 0.0, hi_h = 0.0;
+    double t = -1.0;
+    for (int r = 0; r < LS_ROUNDS; ++r) {
+      if (tid < LS_POINTS) {
+        double tq;
+        if (r == 0) {
+          tq = (double)tid / (double)(LS_POINTS - 1);
+        } else {
+          const double span = hi_t - lo_t;
+          if (tid == 0) tq = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
+          else if (tid == 1) tq = hi_h > 0.0 ? hi_t - hi_f / hi_h : -1.0;
+          else tq = lo_t + span * (double)(tid - 1) / (double)(LS_POINTS - 1);
+          if (!(tq > lo_t && tq < hi_t)) tq = lo_t + span * (tid == 0 ? 0.5 : 0.75);
         }
-        if (!(tA > lo.t && tA < hi.t)) tA = tS;
-        if (!(tB > lo.t && tB < hi.t)) tB = 0.5 * (lo.t + hi.t);
-        if (fabs(tA - tB) <= 1e-12 * tA) tB = 0.5 * (lo.t + tA);
-        LsPoint qA, qB;
-        if (!ls_eval2<VPT>(a, z, w, my_sid, s_tab, s_red, s_i, ls_parity, stride, gdot, Gd, tA, tB,
-                           qA, qB)) { alive = false; break; }
-        if (qA.f == 0.0) { t = qA.t; break; }
-        if (qB.f == 0.0) { t = qB.t; break; }
-        if (qA.f < 0.0 && qA.t > lo.t) lo = qA;
-        if (qA.f > 0.0 && qA.t < hi.t) hi = qA;
-        if (qB.f < 0.0 && qB.t > lo.t) lo = qB;
-        if (qB.f > 0.0 && qB.t < hi.t) hi = qB;
+        s_t[tid] = (float)tq;
       }
-      if (!alive) break;
-      if (t < 0.0) t = lo.t - lo.f * (hi.t - lo.t) / (hi.f - lo.f);
-      t = fmin(fmax(t, lo.t), hi.t);
+      __syncthreads();
+      ++nsync;
+      if (!ls_round<VPT>(a, z, w, my_sid, s_tab, s_t, s_ls, s_res, s_i, ls_parity, stride)) {
+        alive = false;
+        break;
+      }
+      ls_parity ^= 1;
+      // bracket update from the 16 points (identical in every CTA)
+      if (r == 0) {
+        const double f0 = s_res[0] + cg0;
+        const double f1 = s_res[LS_POINTS - 1] + cg0 + cg1;
+        if (!(f0 < 0.0)) { t = 0.0; break; }  // not a descent direction
+        if (f1 <= 0.0) { t = 1.0; break; }
+        lo_f = f0; lo_h = s_res[LS_POINTS] + cg1;
+        hi_f = f1; hi_h = s_res[2 * LS_POINTS - 1] + cg1;
+      }
+      bool exact = false;
+      for (int p = 0; p < LS_POINTS; ++p) {
+        const double tp = (double)s_t[p];
+        const double f = s_res[p] + cg0 + cg1 * tp, h = s_res[LS_POINTS + p] + cg1;
+        if (f == 0.0 && tp > 0.0) { t = tp; exact = true; break; }
+        if (f < 0.0 && tp > lo_t && tp < hi_t) { lo_t = tp; lo_f = f; lo_h = h; }
+        if (f > 0.0 && tp < hi_t && tp > lo_t) { hi_t = tp; hi_f = f; hi_h = h; }
+      }
+      if (exact) break;
+      const double span = hi_t - lo_t;
+      const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
+      const double na = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
+      const double nb = hi_h > 0.0 ? hi_t - hi_f / hi_h : -2.0;
+      // both ends on one linear piece of phi' (their Newton steps agree): exact
+      if (!(span > 0.0) || fabs(na - nb) <= 1e-6 * fabs(tsec) || span <= 1e-7 * hi_t) {
+        t = tsec;
+        break;
+      }
     }
+    if (!alive) break;
+    if (t < 0.0) t = lo_t - lo_f * (hi_t - lo_t) / (hi_f - lo_f);
+    if (!(t >= lo_t)) t = lo_t;
+    t = fmin(t, 1.0);
+    if (timer) { unsigned long long c1 = vmat_globaltimer(); tL += c1 - c0; c0 = c1; }
     if (t <= 0.0) { status = VMAT_ENOTCONV; break; }
 
     // ---------------- update
     for (int s = tid; s < ns; s += nthr) {
-      int k = s_beam[s];
-      double dk = s_d[k];
-      s_dy[s] = t * dk;
-    }
-    __syncthreads();
-    for (int s = tid; s < ns; s += nthr) {
-      int k = s_beam[s];
-      s_y[k] += s_dy[s];
+      const int k = s_beam[s];
+      const double dy = t * s_d[k];
+      s_dy[s] = dy;
+      s_y[k] += dy;
       s_yf[s] = (float)s_y[k];
     }
     const float tf = (float)t;
@@ -466,73 +497,85 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
+#pragma unroll 4
   for (int s = 0; s < ns; ++s) {
     const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
     const float ys = s_yf[s];
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
-      float4 q = __ldg(Ms + tid + nthr * m);
+      const float4 q = __ldg(Ms + tid + nthr * m);
       z[4 * m] = fmaf(q.x, ys, z[4 * m]);
       z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
       z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
       z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]);
     }
   }
-  double cst[1] = {0.0};
+  double cst = 0.0;
 #pragma unroll
   for (int m = 0; m < NG; ++m) {
     float zo[4], fo[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      int v = 4 * m + q;
-      int id = my_sid[v];
+      const int v = 4 * m + q, id = my_sid[v];
       fo[q] = vmat_dF(z[v], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
       zo[q] = z[v];
-      cst[0] += vmat_F((double)z[v], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
+      cst += vmat_F((double)z[v], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
     }
-    size_t off = base + 4 * (tid + (size_t)nthr * m);
+    const size_t off = base + 4 * (tid + (size_t)nthr * m);
     *(float4 *)(a.z_out + off) = make_float4(zo[0], zo[1], zo[2], zo[3]);
     *(float4 *)(a.fp_out + off) = make_float4(fo[0], fo[1], fo[2], fo[3]);
   }
-  block_sum<1>(cst, s_red);
-  if (tid == 0) a.part[(size_t)blockIdx.x * stride + N + 8] = cst[0];
+  cst = warp_sum(cst);
+  if (lane == 0) s_res[32 + warp] = cst;
+  __syncthreads();
+  if (tid == 0) {
+    double c = 0.0;
+    for (int q = 0; q < nwarp; ++q) c += s_res[32 + q];
+    a.part[(size_t)blockIdx.x * stride + COST_OFF(N)] = c;
+  }
+  ++nsync;
   if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) {
     if (blockIdx.x == 0 && tid == 0) a.out->status = VMAT_ETIMEOUT;
     return;
   }
   if (blockIdx.x == 0) {
-    double v[1];
-    grid_gather_sum<1>(a.part, stride, N + 8, v, s_red);
-    if (tid == 0) {
-      double G = 0.0;
-      int npair = a.cyclic ? N : N - 1;
-      for (int k = 0; k < npair; ++k) {
-        int kp = k + 1 < N ? k + 1 : 0;
-        double gap = k + 1 < N ? a.theta[kp] - a.theta[k] : a.theta[0] + 360.0 - a.theta[N - 1];
-        double dd = s_y[kp] - s_y[k];
-        G += dd * dd / gap;
+    if (warp == 0) {
+      double c = 0.0;
+      for (int q = lane; q < (int)gridDim.x; q += 32)
+        c += __ldcg(a.part + (size_t)q * stride + COST_OFF(N));
+      c = warp_sum(c);
+      const double G = G_warp(s_y, a.theta, N, a.cyclic);
+      if (lane == 0) {
+        a.out->cost_active = c;
+        a.out->smooth = G;
+        a.out->rho = rho;
+        a.out->rho0 = rho0;
+        a.out->iters = it;
+        a.out->status = status;
+        if (a.set_rho_plan && a.rho_plan) *a.rho_plan = rho0;
+        if (a.rec_cost) *a.rec_cost = c + a.inactive_cost + a.gamma * G;
+        if (a.rec_rho) *a.rec_rho = rho;
+        if (a.rec_iters) *a.rec_iters = it;
+        if (a.rec_status) *a.rec_status = status;
+        if (a.stats) {
+          a.stats[0] += (double)tA;
+          a.stats[1] += (double)tS;
+          a.stats[2] += (double)tB;
+          a.stats[3] += (double)tL;
+          a.stats[4] += (double)nsync;
+          a.stats[5] += (double)it;
+        }
       }
-      a.out->cost_active = v[0];
-      a.out->smooth = G;
-      a.out->rho = rho;
-      a.out->rho0 = rho0;
-      a.out->iters = it;
-      a.out->status = status;
-      if (a.set_rho_plan && a.rho_plan) *a.rho_plan = rho0;
-      if (a.rec_cost) *a.rec_cost = v[0] + a.inactive_cost + a.gamma * G;
-      if (a.rec_rho) *a.rec_rho = rho;
-      if (a.rec_iters) *a.rec_iters = it;
-      if (a.rec_status) *a.rec_status = status;
     }
     for (int k = tid; k < N; k += nthr) a.y[k] = s_y[k];
   }
 }
 
 // ---------------------------------------------------------------- launch
-static size_t master_smem_bytes(int N, int nthr) {
-  int nwarp = nthr / 32;
-  return (size_t)(5 * N + 9 * 32 + 16) * 8 + (size_t)(2 * N + 768 + nwarp * N) * 4 +
-         (size_t)(8 + N) * 4 + 16;
+static size_t master_smem_bytes(int N, int nthr, int vpt) {
+  const size_t tile = (size_t)nthr * vpt;
+  return (size_t)(5 * N + 32 + 32 + 16 * 32) * 8 +
+         (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + tile * 4 + (size_t)(8 + N) * 4 + 16;
 }
 
 template <int VPT>
@@ -556,7 +599,7 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   if (vpt > 32) return vmat_fail(ctx, VMAT_EINVAL, "too many active voxels for the master kernel");
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
-  size_t smem = master_smem_bytes(ctx->N, nthr);
+  size_t smem = master_smem_bytes(ctx->N, nthr, vpt);
   int nb = 0;
   cudaError_t e = vpt == 4    ? master_occupancy<4>(nthr, smem, &nb)
                   : vpt == 8  ? master_occupancy<8>(nthr, smem, &nb)
@@ -572,6 +615,8 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   ctx->Vpad = (int32_t)(grid * chunk);
   return VMAT_OK;
 }
+
+int64_t vmat_master_scratch(int grid, int N) { return (int64_t)grid * (N + PART_EXTRA) + N; }
 
 vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, double rho_ref,
                                int set_rho_plan, double *rec_cost, double *rec_rho,
@@ -601,15 +646,16 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   a.z_out = ctx->zact;
   a.fp_out = ctx->fpact;
   a.out = ctx->mout;
+  a.stats = ctx->mstats;
   a.rec_cost = rec_cost;
   a.rec_rho = rec_rho;
   a.rec_iters = rec_iters;
   a.rec_status = rec_status;
   a.inactive_cost = ctx->inactive_cost;
   a.wait_ns = 2000000000ull;  // 2 s per grid-wide wait
-  if ((int64_t)ctx->master_grid * (ctx->N + PART_EXTRA) + ctx->N > ctx->red_len)
+  if (vmat_master_scratch(ctx->master_grid, ctx->N) > ctx->red_len)
     return vmat_fail(ctx, VMAT_EINVAL, "reduction scratch too small");
-  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 4, ctx->stream));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, ctx->stream));
   void *args[] = {&a};
   dim3 grid(ctx->master_grid), block(ctx->master_block);
   const void *fn = ctx->master_vpt == 4    ? (const void *)k_master<4>
@@ -650,7 +696,7 @@ extern "C" vmat_status vmat_selftest_grid_wait(vmat_ctx *ctx, int32_t skip_one, 
   int ds = 0;
   VMAT_CUDA(ctx, cudaMemcpyAsync(&ds, ctx->dstatus, 4, cudaMemcpyDeviceToHost, st));
   VMAT_CUDA(ctx, cudaStreamSynchronize(st));
-  // leave the context usable
+  // leave the context usable: a barrier word left mid-count is reset
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->dstatus, 0, 4, st));
   VMAT_CUDA(ctx, cudaStreamSynchronize(st));

@@ -398,13 +398,15 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
     // scratch: master partials [grid][N+16] + reduced gradient [N]; dose
     // partials [ceil(Va/8)] and batched [ceil(Va/8)][32]; 64 result slots at the end
     int64_t nbv = ((int64_t)ctx->Va + 7) / 8 + 1;
-    int64_t need = (int64_t)ctx->master_grid * (N + 16) + N;
+    int64_t need = vmat_master_scratch(ctx->master_grid, N);
     if (nbv * 32 > need) need = nbv * 32;
     ctx->red_len = need + 128;
   }
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->red, ctx->red_len));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->mout, 1));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->bar, 2));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->mstats, 8));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->mstats, 0, 64, st));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->dstatus, 1));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->dstatus, 0, 4, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, st));
@@ -440,7 +442,7 @@ extern "C" void vmat_destroy(vmat_ctx *ctx) {
                   ctx->vm_col, ctx->vm_val, ctx->M, ctx->occ, ctx->lleaf, ctx->rleaf,
                   ctx->slot_beam, ctx->y, ctx->zact, ctx->fpact, ctx->rho_plan, ctx->g,
                   ctx->fgather, ctx->xs, ctx->ap_price, ctx->ap_l, ctx->ap_r, ctx->sel, ctx->sel_l,
-                  ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus};
+                  ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -461,6 +463,14 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
   out->master_grid = ctx->master_grid;
   out->master_block = ctx->master_block;
   out->n_launches = ctx->n_launches;
+  double ms[8] = {0};
+  if (ctx->mstats) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaMemcpy(ms, ctx->mstats, sizeof ms, cudaMemcpyDeviceToHost);
+  }
+  for (int q = 0; q < 4; ++q) out->master_ms[q] = ms[q] * 1e-6;
+  out->master_syncs = (int64_t)ms[4];
+  out->master_pg_iters = (int64_t)ms[5];
   return VMAT_OK;
 }
 

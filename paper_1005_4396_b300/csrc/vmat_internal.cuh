@@ -83,7 +83,8 @@ struct vmat_ctx {
   double *red = nullptr;       // reduction scratch [red_len]
   int64_t red_len = 0;
   MasterOut *mout = nullptr;   // [1]
-  unsigned *bar = nullptr;     // [2] grid barrier counter, generation
+  unsigned *bar = nullptr;     // [2] grid barrier word (+ spare)
+  double *mstats = nullptr;    // [8] cumulative master-kernel phase ns, grid syncs, iterations
   int *dstatus = nullptr;      // [1] sticky device error (VMAT_ETIMEOUT, ...)
 
   // master launch shape
@@ -150,3 +151,4 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
                                      double *cost_dev);
 vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G);
 vmat_status vmat_configure_master(vmat_ctx *ctx);
+int64_t vmat_master_scratch(int grid, int N);

@@ -48,7 +48,8 @@ class vmat_info(ctypes.Structure):
     _fields_ = [("n_vox", _i32), ("n_active", _i32), ("n_angles", _i32), ("n_rows", _i32),
                 ("n_cols", _i32), ("n_beamlets", _i64), ("nnz", _i64), ("n_columns", _i32),
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
-                ("master_block", _i32), ("n_launches", _i64)]
+                ("master_block", _i32), ("n_launches", _i64), ("master_ms", _d * 4),
+                ("master_syncs", _i64), ("master_pg_iters", _i64)]
 
 
 class vmat_column(ctypes.Structure):
@@ -171,7 +172,9 @@ def vmat_destroy(ctx):
 def vmat_get_info(ctx) -> dict:
     inf = vmat_info()
     _check(ctx, load_library().vmat_get_info(ctx, ctypes.byref(inf)))
-    return {k: getattr(inf, k) for k, _ in vmat_info._fields_}
+    out = {k: getattr(inf, k) for k, _ in vmat_info._fields_}
+    out["master_ms"] = list(out["master_ms"])
+    return out
 
 
 def vmat_dose(ctx, x, z=None, fprime=None, want_cost=True):
