@@ -220,6 +220,36 @@ VMAT_API vmat_status vmat_dose_batch32(vmat_ctx *ctx, const float *X_dev, float 
  * [n_vox][32] float, G_dev [B][32] float. */
 VMAT_API vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, float *G_dev);
 
+/* Dose and voxel cost without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not let a
+ * library allocate GPU memory (a host framework that owns a fixed device pool
+ * and forbids cudaMalloc behind its back, a service that may not allocate
+ * while it serves plans, an embedded integration that sizes every buffer up
+ * front).  It needs no context: the caller passes the voxel-major D as CSR
+ * over its n_vox voxels (row_ptr_dev [n_vox+1] int64, beamlet_dev [nnz]
+ * int32 beamlet of each entry, val_dev [nnz] float D_ij), the fluence x_dev
+ * [B] float, struct_id_dev [n_vox] uint8 (< n_struct) and params_dev
+ * [3*n_struct] double (all T, then all alpha, then all beta of Eq. 1), and
+ * gets z_dev [n_vox] float and fprime_dev [n_vox] float F'(z) (either may be
+ * NULL) and cost_dev [1] double = sum_j F(z_j) reduced in FP64 in a fixed
+ * order.  Everything is enqueued on cuda_stream (a cudaStream_t, NULL: legacy
+ * default stream) and the call returns without waiting.
+ * Its only scratch, one FP64 partial cost per 8 voxels, is a file-scope
+ * __device__ array of 65,536 doubles (512 KiB) that every GPU loading the
+ * library keeps until the process exits; n_vox above 524,288 is rejected
+ * with VMAT_EINVAL.  All calls share that array and it keeps the last call's
+ * contents, so calls that may overlap on the GPU (different streams, or
+ * different threads) race and must be serialised by the caller.  The first
+ * call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Errors are
+ * reported by vmat_last_error(NULL). */
+VMAT_API vmat_status vmat_dose_cost_noalloc(int32_t n_vox, const int64_t *row_ptr_dev,
+                                            const int32_t *beamlet_dev, const float *val_dev,
+                                            const float *x_dev, const uint8_t *struct_id_dev,
+                                            const double *params_dev, int32_t n_struct,
+                                            float *z_dev, float *fprime_dev, double *cost_dev,
+                                            void *cuda_stream);
+
 /* Self-test of the bounded device waits (no counterpart in the method):
  * launches the master kernel's grid barrier with every CTA but one waiting
  * for a CTA that never arrives, each wait limited to wait_seconds.  Returns

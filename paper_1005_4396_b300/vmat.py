@@ -84,6 +84,7 @@ EXPORTS = {
     "vmat_price_batch32": [_p, _p, _p],
     "vmat_selftest_grid_wait": [_p, _i32, _d],
     "vmat_set_profiling": [_p, _i32],
+    "vmat_dose_cost_noalloc": [_i32, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p, _p],
 }
 
 _lib = None
@@ -259,6 +260,17 @@ def vmat_dose_batch32(ctx, X, Z, fprime=None, want_cost=True):
 
 def vmat_price_batch32(ctx, Fp, G):
     _check(ctx, load_library().vmat_price_batch32(ctx, _ptr(Fp), _ptr(G)))
+
+
+def vmat_dose_cost_noalloc(n_vox, row_ptr, beamlet, val, x, struct_id, params, n_struct,
+                           z=None, fprime=None, cost=None, stream=None):
+    """Dose + voxel cost with no device allocation by the library (tensors
+    are the caller's; see include/vmat.h).  Enqueued on `stream`."""
+    st = load_library().vmat_dose_cost_noalloc(
+        int(n_vox), _ptr(row_ptr), _ptr(beamlet), _ptr(val), _ptr(x), _ptr(struct_id),
+        _ptr(params), int(n_struct), _ptr(z), _ptr(fprime), _ptr(cost), stream)
+    if st != VMAT_OK:
+        raise VmatError(st, load_library().vmat_last_error(None).decode())
 
 
 def vmat_set_profiling(ctx, on):
