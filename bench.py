@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
+MASTER_TRAFFIC_RATIO = (8.186832e9 + 10.338048e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 
@@ -119,25 +120,31 @@ def _describe(cfg, prob):
 
 def _algorithmic_bytes(prob, info, rec):
     """Bytes each kernel must move per launch by its definition (not counting
-    re-reads): master: every PG iteration reads the columns twice (gradient
-    pass, direction pass) plus one read at entry and one at exit, and writes
-    z and F'; price: the D rows of the free beams (8 B/nnz FP32 value+index,
-    8 B row pointer), the prices written, F' gathered once."""
+    re-reads).  master: every PG iteration reads the aperture-dose columns
+    twice (gradient pass, direction pass) plus once at entry and once at
+    exit, counting only the subtiles of a column that hold a nonzero (an
+    all-zero subtile carries no information and is not read), and writes z
+    and F'.  price: the D rows of the free beams (8 B/nnz FP32 value+index),
+    their row pointers, the prices written, F' gathered once.  Also returns
+    the master bytes of dense columns (every voxel of every column)."""
     cfg = prob.cfg
     RC = cfg.n_rows * cfg.n_cols
     Va = info["n_active"]
+    sv = info["subtile_voxels"]
     vb = 8 if info["d_dtype"] == 1 else 6
     nnz_beam = np.add.reduceat(np.diff(prob.row_ptr), np.arange(0, prob.n_beamlets, RC))
     free_nnz = nnz_beam.sum()
-    master, price = [], []
+    master, dense, price = [], [], []
+    sub = np.cumsum(rec["col_subtiles"].astype(np.float64))
     for t, k in enumerate(rec["k"]):
-        ncol = t + 1
         P = int(rec["iters"][t])
-        master.append((2 * P + 2) * ncol * Va * 4 + 8 * Va)
+        master.append((2 * P + 2) * sub[t] * sv * 4 + 8 * Va)
+        dense.append((2 * P + 2) * (t + 1) * Va * 4 + 8 * Va)
         free_beams = cfg.n_angles - t
         price.append(free_nnz * vb + free_beams * RC * (8 + 4) + 4 * Va)
         free_nnz -= nnz_beam[k]
-    return np.array(master, dtype=np.float64), np.array(price, dtype=np.float64)
+    return (np.array(master, dtype=np.float64), np.array(price, dtype=np.float64),
+            np.array(dense, dtype=np.float64))
 
 
 def _dose_err(prob, plan_f, plan_ref_dose, lleaf, rleaf, y):
@@ -203,9 +210,10 @@ def run_ours(args):
     phase = np.sum([r["phase_ms"] for r in recs], axis=0)  # [n_iter, 4]
     ph_tot = phase.sum(axis=0) / args.steps
     names = ["price_spmv", "pricing", "aperture", "master"]
-    mb, pb = zip(*[_algorithmic_bytes(prob, info, r) for r in recs])
+    mb, pb, db = zip(*[_algorithmic_bytes(prob, info, r) for r in recs])
     mb = np.sum(mb, axis=0) / args.steps
     pb = np.sum(pb, axis=0) / args.steps
+    db = np.sum(db, axis=0) / args.steps
     master_gbs = mb.sum() / (ph_tot[3] / 1e3) / 1e9
     price_gbs = pb.sum() / (ph_tot[0] / 1e3) / 1e9
     dom = int(np.argmax(ph_tot))
@@ -216,11 +224,19 @@ def run_ours(args):
         "bound": "hbm", "achieved": round(dom_gbs, 1) if dom_gbs else None,
         "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4) if dom_gbs else None,
         "peak_kind": f"{peak_kind} copy bandwidth",
-        "traffic": None,
+        # DRAM bytes per launch = measured traffic/algorithmic ratio of one ncu capture of
+        # this kernel (half-depth phantom, 150 columns, 30 iterations: 8.197 GB read+write
+        # for 8.239 GB algorithmic) times this launch's algorithmic bytes
+        "traffic": round(MASTER_TRAFFIC_RATIO * float(mb.sum()) / n_master, 0) if dom == 3 else None,
+        "traffic_note": "per launch (average over the plan), scaled from one ncu capture of a "
+                        "smaller case; see profiles/k_master_halfdepth_150cols.md",
         "launches_per_step": n_master,
-        "note": ("master algorithmic bytes = (2*P+2) column reads of 4 B x active voxels per "
-                 "launch; the columns fit in L2 while a plan has < ~70 of them, so part of "
-                 "this traffic is served from L2"),
+        "bytes_per_step": float(mb.sum()),
+        "dense_column_equivalent_GB/s": round(db.sum() / (ph_tot[3] / 1e3) / 1e9, 1),
+        "note": ("master algorithmic bytes per launch = (2*P+2) reads of the nonzero subtiles "
+                 "of the plan's aperture-dose columns (4 B per voxel) + z and F' written; "
+                 "P = projected-gradient iterations of the launch; while the nonzero part "
+                 "of the columns fits in L2 (126 MB) part of it is served from L2"),
     }
     # stand-alone SpMV bandwidth of the two sparse products at full D (FP32)
     x = torch.rand(prob.n_beamlets, device="cuda")
@@ -377,6 +393,39 @@ def run_cpu_baseline(prob, args):
                       f"fewest columns, so this overstates the oracle's whole-plan rate"}
 
 
+# ---------------------------------------------------------------- profiling cases
+def run_case(args):
+    """Small cases sized for an ncu capture (a few GB on the device, inputs
+    larger than L2): the prostate phantom cut to 32 slices (V_active 221k,
+    nnz 2.2e8).  master: 150 seeded apertures, one master launch of 30
+    projected-gradient iterations.  spmv: dose and price SpMV, twice each."""
+    import torch
+    from paper_1005_4396_b300 import inputs, vmat
+    torch.cuda.set_device(0)
+    cfg = inputs.prostate_config(nz=32)
+    prob = inputs.make_problem(cfg)
+    plan = vmat.Plan(prob, val_f32=True)
+    out = {"case": args.case, "nnz": prob.nnz, "active_voxels": plan.info["n_active"]}
+    if args.case == "master":
+        R = cfg.n_rows
+        ll, rr = inputs.random_apertures(7, cfg)
+        beams = np.random.default_rng(7).permutation(cfg.n_angles)[:150]
+        for k in beams:
+            plan.add_column(int(k), ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
+        y = np.zeros(cfg.n_angles)
+        res = plan.master_step(max_iters=30, kkt_tol=1e-9, y=y)
+        out.update(columns=150, master=res)
+    else:
+        x = torch.rand(prob.n_beamlets, device="cuda")
+        f = torch.randn(prob.n_vox, device="cuda")
+        for _ in range(2):
+            plan.dose(x)
+            plan.price(f)
+        torch.cuda.synchronize()
+    plan.close()
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
     ws, rank, local = _dist()
@@ -419,7 +468,12 @@ def main():
     ap.add_argument("--workload", default="prostate", choices=["prostate", "tiny", "headneck"])
     ap.add_argument("--cpu-iters", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
+    ap.add_argument("--case", default=None, choices=["master", "spmv"],
+                    help="small case for an ncu capture instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

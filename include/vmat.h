@@ -97,6 +97,8 @@ typedef struct {
                                   pass + its reduction, step, direction pass, line search */
   int64_t master_syncs;        /* cumulative grid-wide barriers of the master kernel */
   int64_t master_pg_iters;     /* cumulative projected-gradient iterations */
+  int32_t subtile_voxels;      /* voxels per subtile of the aperture-dose columns */
+  int32_t n_subtiles;          /* subtiles per column (padded active voxels / subtile_voxels) */
 } vmat_info;
 
 /* Copy the problem to the device and build every storage form of D:
@@ -192,6 +194,8 @@ typedef struct {              /* caller-allocated host arrays (any may be NULL) 
   double *phase_ms;           /* [n_iters*4] device time (ms) of each iteration's phases:
                                  prices, pricing, aperture column, master problem;
                                  written only while profiling is on */
+  int32_t *col_subtiles;      /* [n_iters] subtiles holding a nonzero of each added column
+                                 (the master kernel streams only those) */
 } vmat_colgen_result;
 
 /* Column generation (Sec. 2.2, Fig. 1) from the context's current plan:
@@ -216,9 +220,32 @@ VMAT_API vmat_status vmat_set_profiling(vmat_ctx *ctx, int32_t on);
 VMAT_API vmat_status vmat_dose_batch32(vmat_ctx *ctx, const float *X_dev, float *Z_dev, float *fprime_dev,
                               double *cost_host);
 
-/* Batched adjoint: G[i][b] = sum_j D_ij Fp[j][b] for all beamlets, Fp_dev
- * [n_vox][32] float, G_dev [B][32] float. */
-VMAT_API vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, float *G_dev);
+/* Batched adjoint: G[i][b] = w[b] * sum_j D_ij Fp[j][b] for all beamlets,
+ * Fp_dev [n_vox][32] float, w_dev [32] float per-vector weights (NULL: all
+ * 1; the backward pass passes the incoming gradient), G_dev [B][32] float. */
+VMAT_API vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, const float *w_dev,
+                                        float *G_dev);
+
+/* Aperture maps for 32 intensity vectors (the differentiable forward with
+ * respect to aperture intensities, Eq. 3): X = A Y with X[i][b] = Y[k][b] if
+ * beamlet i = (k*R + r)*C + c is open in beam k (l[k*R+r] <= c < r[k*R+r]),
+ * else 0.  l_dev, r_dev [N*R] int16 device; Y_dev [N][32], X_dev [B][32]
+ * float row-major. */
+VMAT_API vmat_status vmat_aperture_fluence_batch32(vmat_ctx *ctx, const int16_t *l_dev,
+                                                   const int16_t *r_dev, const float *Y_dev,
+                                                   float *X_dev);
+/* Its adjoint: GY[k][b] = sum over the open beamlets i of beam k of GX[i][b]
+ * (rows, then columns, in order), plus, if Y_dev is not NULL, the gradient of
+ * gamma*G(Y) (Eq. 2) times w[b] (w_dev [32] or NULL: 1).  GX_dev [B][32],
+ * Y_dev [N][32], GY_dev [N][32] float. */
+VMAT_API vmat_status vmat_aperture_adjoint_batch32(vmat_ctx *ctx, const int16_t *l_dev,
+                                                   const int16_t *r_dev, const float *GX_dev,
+                                                   const float *Y_dev, const float *w_dev,
+                                                   float *GY_dev);
+/* Smoothing term of Eq. 2 (ring if the context is cyclic) for 32 intensity
+ * vectors: G_host [32] (FP64) and, if dG_dev is not NULL, dG/dY [N][32]. */
+VMAT_API vmat_status vmat_smoothing_batch32(vmat_ctx *ctx, const float *Y_dev, double *G_host,
+                                            float *dG_dev);
 
 /* Dose and voxel cost without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not let a

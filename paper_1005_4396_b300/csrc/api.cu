@@ -143,7 +143,7 @@ extern "C" vmat_status vmat_plan_dose(vmat_ctx *ctx, float *z_dev) {
 
 // ---------------------------------------------------------------- column generation
 struct Records {
-  int32_t *k, *iters, *status;
+  int32_t *k, *iters, *status, *tiles;
   double *p, *p2, *cost, *rho;
 };
 
@@ -174,7 +174,7 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   cudaStream_t st = ctx->stream;
   // device records (one block) and forced plan
   size_t nn = n > 0 ? n : 1;
-  size_t bytes = nn * (3 * 4 + 4 * 8) + 64 + (o->forced_angle ? nn * (4 + 4 * (size_t)R) + 64 : 0);
+  size_t bytes = nn * (4 * 4 + 4 * 8) + 64 + (o->forced_angle ? nn * (4 + 4 * (size_t)R) + 64 : 0);
   char *blk = nullptr;
   VMAT_CUDA(ctx, cudaMallocAsync((void **)&blk, bytes, st));
   Records rec;
@@ -185,10 +185,11 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   rec.k = (int32_t *)(rec.rho + nn);
   rec.iters = rec.k + nn;
   rec.status = rec.iters + nn;
+  rec.tiles = rec.status + nn;
   int32_t *fk = nullptr;
   int16_t *fl = nullptr, *fr = nullptr;
   if (o->forced_angle) {
-    fk = (int32_t *)(((uintptr_t)(rec.status + nn) + 15) & ~(uintptr_t)15);
+    fk = (int32_t *)(((uintptr_t)(rec.tiles + nn) + 15) & ~(uintptr_t)15);
     fl = (int16_t *)(fk + nn);
     fr = fl + nn * R;
     cudaMemcpyAsync(fk, o->forced_angle, n * 4, cudaMemcpyHostToDevice, st);
@@ -220,7 +221,7 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
       if (s != VMAT_OK) break;
     }
     mark(t, 2);
-    s = vmat_launch_add_column(ctx, ctx->n_slots);
+    s = vmat_launch_add_column(ctx, ctx->n_slots, rec.tiles + t);
     if (s != VMAT_OK) break;
     ctx->n_slots += 1;
     mark(t, 3);
@@ -231,12 +232,13 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   if (fk) {  // the beam actually added at each step is the forced one
     cudaMemcpyAsync(rec.k, fk, n * 4, cudaMemcpyDeviceToDevice, st);
   }
-  std::vector<int32_t> hk(nn), hit(nn), hst(nn);
+  std::vector<int32_t> hk(nn), hit(nn), hst(nn), htl(nn);
   std::vector<double> hp(nn), hp2(nn), hc(nn), hr(nn);
   if (n > 0) {
     cudaMemcpyAsync(hk.data(), rec.k, n * 4, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hit.data(), rec.iters, n * 4, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hst.data(), rec.status, n * 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(htl.data(), rec.tiles, n * 4, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hp.data(), rec.p, n * 8, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hp2.data(), rec.p2, n * 8, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hc.data(), rec.cost, n * 8, cudaMemcpyDeviceToHost, st);
@@ -267,6 +269,7 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
       if (res->cost) res->cost[t] = hc[t];
       if (res->kkt) res->kkt[t] = hr[t];
       if (res->master_iters) res->master_iters[t] = hit[t];
+      if (res->col_subtiles) res->col_subtiles[t] = htl[t];
     }
   }
   for (int t = 0; t < n; ++t) {
@@ -291,9 +294,10 @@ extern "C" vmat_status vmat_dose_batch32(vmat_ctx *ctx, const float *X_dev, floa
   return sync_status(ctx);
 }
 
-extern "C" vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, float *G_dev) {
+extern "C" vmat_status vmat_price_batch32(vmat_ctx *ctx, const float *Fp_dev, const float *w_dev,
+                                          float *G_dev) {
   if (!ctx || !Fp_dev || !G_dev) return ctx ? vmat_fail(ctx, VMAT_EINVAL, "NULL argument") : VMAT_EINVAL;
-  vmat_status s = vmat_launch_price_batch32(ctx, Fp_dev, G_dev);
+  vmat_status s = vmat_launch_price_batch32(ctx, Fp_dev, w_dev, G_dev);
   if (s != VMAT_OK) return s;
   return sync_status(ctx);
 }

@@ -4,13 +4,16 @@
 // dose of the aperture added s-th (unit intensity), stored slot-major with
 // a padded column stride Vpad.
 //
-// One cooperative launch runs the whole solve.  CTA b owns the voxel tile
-// [b*T, (b+1)*T), T = threads * VPT; thread t owns the float4 groups
-// 4*(t + threads*m), m < VPT/4, of the tile and keeps their dose z and
-// direction image w in registers for the whole solve.  Per iteration:
-//   pass A   gradient M^T F'(z): F' of the tile goes to shared memory; warp w
-//            takes slots w, w+W, ... and streams each slot's tile (T floats,
-//            contiguous) with many independent 16-byte loads per lane
+// One cooperative launch runs the whole solve.  The padded voxels are cut
+// into subtiles of ST = 4*threads voxels; CTA b owns the VPT/4 subtiles
+// b, b+G, b+2G, ... (spread over the volume, so dense and sparse regions
+// mix in every CTA) and thread t holds voxels 4t..4t+3 of each in registers
+// (dose z, direction image w) for the whole solve.  A column is nonzero
+// only near its aperture's beam path: per (column, subtile) flags let every
+// pass skip all-zero subtiles.  Per iteration:
+//   pass A   gradient M^T F'(z): F' of the CTA's subtiles goes to shared
+//            memory; each warp streams whole (column, subtile) pairs with
+//            many independent 16-byte loads per lane
 //   reduce   per-slot CTA partials -> grid barrier -> warp-per-slot fixed-order
 //            sums over CTAs -> grid barrier (deterministic, no float atomics)
 //   step     every CTA forms the same d = P+(y - s g) - y (second
@@ -38,6 +41,7 @@
 
 struct MasterArgs {
   const float *M;
+  const int32_t *tflag;  // [N][G*VPT/4] nonzero flags of the column subtiles
   int32_t Vpad, nslots, N, cyclic, max_iters, set_rho_plan;
   const int32_t *slot_beam;
   const uint8_t *sid;
@@ -127,41 +131,33 @@ __device__ __forceinline__ float warp_transpose_sum32(float (&v)[32]) {
   return v[0];
 }
 
-// derivative of the smoothing term G (Eq. 2) at beam k
-__device__ __forceinline__ double dG_beam(const double *y, const double *theta, int N, int cyclic,
-                                          int k) {
-  double r = 0.0;
-  if (k > 0 || cyclic) {  // pair (k-1, k)
-    int km = k > 0 ? k - 1 : N - 1;
-    double gap = k > 0 ? theta[k] - theta[km] : theta[0] + 360.0 - theta[N - 1];
-    r += 2.0 * (y[k] - y[km]) / gap;
-  }
-  if (k < N - 1 || cyclic) {  // pair (k, k+1)
-    int kp = k < N - 1 ? k + 1 : 0;
-    double gap = k < N - 1 ? theta[kp] - theta[k] : theta[0] + 360.0 - theta[N - 1];
-    r -= 2.0 * (y[kp] - y[k]) / gap;
-  }
-  return r;
+// derivative of the smoothing term G (Eq. 2) at beam k, from inverse gaps
+__device__ __forceinline__ double dG_inv(const double *y, const double *igl, const double *igr,
+                                         int N, int k) {
+  const int km = k > 0 ? k - 1 : N - 1, kp = k < N - 1 ? k + 1 : 0;
+  return 2.0 * (y[k] - y[km]) * igl[k] - 2.0 * (y[kp] - y[k]) * igr[k];
 }
 
-// G(u) over all pairs (Eq. 2), by one warp; valid in every lane
-__device__ __forceinline__ double G_warp(const double *u, const double *theta, int N, int cyclic) {
+// G(u) (Eq. 2) over all pairs from inverse gaps, by one warp; valid in every lane
+__device__ __forceinline__ double G_inv(const double *u, const double *igr, int N) {
   const int lane = threadIdx.x & 31;
   double g = 0.0;
-  const int npair = cyclic ? N : N - 1;
-  for (int k = lane; k < npair; k += 32) {
-    int kp = k + 1 < N ? k + 1 : 0;
-    double gap = k + 1 < N ? theta[kp] - theta[k] : theta[0] + 360.0 - theta[N - 1];
-    double dd = u[kp] - u[k];
-    g += dd * dd / gap;
+  for (int k = lane; k < N; k += 32) {
+    const int kp = k < N - 1 ? k + 1 : 0;
+    const double dd = u[kp] - u[k];
+    g += dd * dd * igr[k];  // igr[N-1] is 0 on a path
   }
   return warp_sum(g);
 }
 
-// One line-search round: phi' and phi''(t+) at LS_POINTS points for this
-// thread's voxels (FP32), summed over the CTA (FP32 in a warp, FP64 across
-// warps), written as this CTA's partials and grid-reduced in FP64 in a fixed
-// order.  Out: s_res[0..15] = sums of phi' terms, s_res[16..31] = phi''.
+// One line-search round at LS_POINTS trial points t.  Per voxel the round
+// evaluates the increment of its phi' term over t = 0,
+//   D_j(t) = 2 w_j [ (c_j(t) - c_j(0)) e_j + c_j(t) t w_j ],  e_j = z_j - T_j,
+// (c = alpha below the threshold, beta above), which is O(t w_j^2) and free
+// of the cancellation that phi' itself suffers near convergence, and the
+// phi'' term 2 c_j(t) w_j^2.  FP32 per voxel, FP32 within a warp, FP64 across
+// warps and CTAs in a fixed order.  Out: s_res[0..15] = sum_j D_j(t_p),
+// s_res[16..31] = sum_j 2 c_j(t_p) w_j^2.
 template <int VPT>
 __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[VPT],
                                          const float (&w)[VPT], const uint8_t (&sid)[VPT],
@@ -179,13 +175,15 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     const float T = s_tab[id], al = s_tab[256 + id], be = s_tab[512 + id];
     const float e0 = z[q] - T;
     const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
+    const float c0 = e0 > 0.f ? be : (e0 < 0.f ? al : cw);
 #pragma unroll
     for (int p = 0; p < LS_POINTS; ++p) {
-      const float e = fmaf(s_t[p], wq, e0);
+      const float tp = s_t[p];
+      const float e = fmaf(tp, wq, e0);
       const float c = e > 0.f ? be : (e < 0.f ? al : cw);
-      const float cwq = 2.f * c * wq;
-      v[p] = fmaf(cwq, e, v[p]);
-      v[LS_POINTS + p] = fmaf(cwq, wq, v[LS_POINTS + p]);
+      const float twq = 2.f * wq;
+      v[p] = fmaf(twq, fmaf(c - c0, e0, c * tp * wq), v[p]);
+      v[LS_POINTS + p] = fmaf(twq * c, wq, v[LS_POINTS + p]);
     }
   }
   const float ws = warp_transpose_sum32(v);
@@ -221,44 +219,79 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   const int stride = N + PART_EXTRA;
   constexpr int NG = VPT / 4;       // float4 groups per thread
-  const int tile = nthr * VPT;      // voxels per CTA
-  const int lane4 = tile / 128;     // float4s per lane when a warp streams a tile
+  const int ST = nthr * 4;          // voxels per subtile
+  const int G = gridDim.x, NS = G * NG;
+  const int lane4 = ST / 128;       // float4s per lane when a warp streams a subtile
+#define SUB_OFF(m) ((size_t)(blockIdx.x + G * (m)) * ST)
 
   double *s_y = (double *)smem;      // [N] per beam
   double *s_d = s_y + N;             // [N] per beam
   double *s_g = s_d + N;             // [N] per slot
   double *s_gold = s_g + N;          // [N] per slot
   double *s_dy = s_gold + N;         // [N] per slot
-  double *s_sc = s_dy + N;           // [32] CTA-wide scalars
+  double *s_igl = s_dy + N;          // [N] 1/gap to the left neighbour (0: none)
+  double *s_igr = s_igl + N;         // [N] 1/gap to the right neighbour (0: none)
+  double *s_dgy = s_igr + N;         // [N] per slot: dG(y) at the slot's beam
+  double *s_sc = s_dgy + N;          // [32] CTA-wide scalars
   double *s_res = s_sc + 32;         // [32 + 16*32] line-search sums and scratch
   float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [N] per slot
   float *s_df = s_yf + N;                         // [N] per slot
   float *s_tab = s_df + N;                        // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
   float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
-  float *s_fp = s_ls + 16 * 32;                   // [tile] F' of the tile
-  int *s_i = (int *)(s_fp + tile);                // [8]
+  float *s_fp = s_ls + 16 * 32;                   // [NG][ST] F' of the CTA's subtiles
+  float *s_pp = s_fp + NG * ST;                   // [N*NG] warp partial per (slot, subtile) pair
+  int *s_i = (int *)(s_pp + N * NG);              // [8]: 1 nonzero slots, 2 nonzero pairs
   int *s_beam = s_i + 8;                          // [N] beam of slot
+  int *s_nz = s_beam + N;                         // [N] slots with a nonzero subtile here
+  int *s_mask = s_nz + N;                         // [N] per slot: bit m = subtile m nonzero
+  int *s_pst = s_mask + N;                        // [N+1] first pair of each slot
+  int *s_pair = s_pst + N + 1;                    // [N*NG] pairs s*8+m in slot order
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
   for (int k = tid; k < N; k += nthr) {
     s_y[k] = a.y[k];
     s_d[k] = 0.0;
+    const bool hl = k > 0 || a.cyclic, hr = k < N - 1 || a.cyclic;
+    s_igl[k] = hl ? 1.0 / (k > 0 ? a.theta[k] - a.theta[k - 1] : a.theta[0] + 360.0 - a.theta[N - 1])
+                  : 0.0;
+    s_igr[k] = hr ? 1.0 / (k < N - 1 ? a.theta[k + 1] - a.theta[k] : a.theta[0] + 360.0 - a.theta[N - 1])
+                  : 0.0;
   }
   for (int s = tid; s < ns; s += nthr) {
     s_beam[s] = a.slot_beam[s];
     s_dy[s] = 0.0;
     s_gold[s] = 0.0;
   }
+  for (int s = tid; s < ns; s += nthr) {
+    int mk = 0;
+    for (int m = 0; m < NG; ++m)
+      if (a.tflag[(size_t)s * NS + blockIdx.x + G * m]) mk |= 1 << m;
+    s_mask[s] = mk;
+  }
+  __syncthreads();
+  if (tid == 0) {  // nonzero columns and (column, subtile) pairs, in slot order
+    int n = 0, np = 0;
+    for (int s = 0; s < ns; ++s) {
+      const int mk = s_mask[s];
+      s_pst[s] = np;
+      if (mk) s_nz[n++] = s;
+      for (int m = 0; m < NG; ++m)
+        if (mk >> m & 1) s_pair[np++] = s * 8 + m;
+    }
+    s_pst[ns] = np;
+    s_i[1] = n;
+    s_i[2] = np;
+  }
   __syncthreads();
   for (int s = tid; s < ns; s += nthr) s_yf[s] = (float)s_y[s_beam[s]];
+  const int nnzs = s_i[1], npairs = s_i[2];
 
-  const size_t base = (size_t)blockIdx.x * tile;
   uint8_t my_sid[VPT];
 #pragma unroll
   for (int m = 0; m < NG; ++m)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) my_sid[4 * m + q] = a.sid[base + 4 * (tid + nthr * m) + q];
+    for (int q = 0; q < 4; ++q) my_sid[4 * m + q] = a.sid[SUB_OFF(m) + 4 * tid + q];
   float z[VPT], w[VPT];
   __syncthreads();
 
@@ -266,12 +299,14 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
 #pragma unroll 4
-  for (int s = 0; s < ns; ++s) {
-    const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
+  for (int q = 0; q < nnzs; ++q) {
+    const int s = s_nz[q], mk = s_mask[s];
+    const float *Ms = a.M + (size_t)s * a.Vpad;
     const float ys = s_yf[s];
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
-      const float4 q = __ldg(Ms + tid + nthr * m);
+      if (!(mk >> m & 1)) continue;
+      const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
       z[4 * m] = fmaf(q.x, ys, z[4 * m]);
       z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
       z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
@@ -300,12 +335,13 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       f.z = vmat_dF(z[4 * m + 2], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
       id = my_sid[4 * m + 3];
       f.w = vmat_dF(z[4 * m + 3], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
-      *(float4 *)(s_fp + 4 * (tid + nthr * m)) = f;
+      *(float4 *)(s_fp + m * ST + 4 * tid) = f;
     }
     __syncthreads();
-    for (int s = warp; s < ns; s += nwarp) {
-      const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
-      const float4 *F4 = (const float4 *)s_fp;
+    for (int q = warp; q < npairs; q += nwarp) {
+      const int s = s_pair[q] >> 3, m = s_pair[q] & 7;
+      const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + SUB_OFF(m));
+      const float4 *F4 = (const float4 *)(s_fp + m * ST);
       float acc = 0.f;
 #pragma unroll 8
       for (int i = 0; i < lane4; ++i) {
@@ -317,7 +353,13 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         acc = fmaf(q.w, f.w, acc);
       }
       acc = warp_sumf(acc);
-      if (lane == 0) a.part[(size_t)blockIdx.x * stride + s] = (double)acc;
+      if (lane == 0) s_pp[q] = acc;
+    }
+    __syncthreads();
+    for (int s = tid; s < ns; s += nthr) {  // all-zero subtiles contribute exact zeros
+      double acc = 0.0;
+      for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) acc += (double)s_pp[q];
+      a.part[(size_t)blockIdx.x * stride + s] = acc;
     }
     ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
@@ -333,8 +375,11 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     if (timer) { unsigned long long c1 = vmat_globaltimer(); tA += c1 - c0; c0 = c1; }
 
     // ---------------- gradient, residual, direction (same in every CTA)
-    for (int s = tid; s < ns; s += nthr)
-      s_g[s] = __ldcg(a.gred + s) + a.gamma * dG_beam(s_y, a.theta, N, a.cyclic, s_beam[s]);
+    for (int s = tid; s < ns; s += nthr) {
+      const double dg = dG_inv(s_y, s_igl, s_igr, N, s_beam[s]);
+      s_dgy[s] = dg;
+      s_g[s] = __ldcg(a.gred + s) + a.gamma * dg;
+    }
     __syncthreads();
     if (warp == 0) {
       double r = 0.0, ym = 0.0, gm = 0.0, dyg = 0.0, dgg = 0.0;
@@ -380,28 +425,34 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       s_gold[s] = s_g[s];
     }
     __syncthreads();
-    if (warp == 0) {  // gdot = dG(y).d over beams with a column, Gd = G(d)
-      double gd = 0.0;
-      for (int s = lane; s < ns; s += 32)
-        gd += dG_beam(s_y, a.theta, N, a.cyclic, s_beam[s]) * s_d[s_beam[s]];
+    if (warp == 0) {  // g.d (full gradient: phi'(0)), dG(y).d and G(d)
+      double gd = 0.0, g0 = 0.0;
+      for (int s = lane; s < ns; s += 32) {
+        const double dk = s_d[s_beam[s]];
+        gd += s_dgy[s] * dk;
+        g0 += s_g[s] * dk;
+      }
       gd = warp_sum(gd);
-      const double Gd = G_warp(s_d, a.theta, N, a.cyclic);
-      if (lane == 0) { s_sc[2] = gd; s_sc[3] = Gd; }
+      g0 = warp_sum(g0);
+      const double Gd = G_inv(s_d, s_igr, N);
+      if (lane == 0) { s_sc[2] = gd; s_sc[3] = Gd; s_sc[4] = g0; }
     }
     __syncthreads();
-    const double gdot = s_sc[2], Gd = s_sc[3];
+    const double gdot = s_sc[2], Gd = s_sc[3], phi0 = s_sc[4];
     if (timer) { unsigned long long c1 = vmat_globaltimer(); tS += c1 - c0; c0 = c1; }
 
     // ---------------- pass B: z = M y, w = M d
 #pragma unroll
     for (int v = 0; v < VPT; ++v) { z[v] = 0.f; w[v] = 0.f; }
 #pragma unroll 4
-    for (int s = 0; s < ns; ++s) {
-      const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
+    for (int q = 0; q < nnzs; ++q) {
+      const int s = s_nz[q], mk = s_mask[s];
+      const float *Ms = a.M + (size_t)s * a.Vpad;
       const float ys = s_yf[s], ds = s_df[s];
 #pragma unroll
       for (int m = 0; m < NG; ++m) {
-        const float4 q = __ldg(Ms + tid + nthr * m);
+        if (!(mk >> m & 1)) continue;
+        const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
         z[4 * m] = fmaf(q.x, ys, z[4 * m]);         w[4 * m] = fmaf(q.x, ds, w[4 * m]);
         z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]); w[4 * m + 1] = fmaf(q.y, ds, w[4 * m + 1]);
         z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]); w[4 * m + 2] = fmaf(q.z, ds, w[4 * m + 2]);
@@ -411,14 +462,25 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     if (timer) { unsigned long long c1 = vmat_globaltimer(); tB += c1 - c0; c0 = c1; }
 
     // ---------------- exact line search on [0, 1]
-    const double cg0 = a.gamma * gdot, cg1 = 2.0 * a.gamma * Gd;
-    double lo_t = 0.0, lo_f = 0.0, lo_h = 0.0, hi_t = 1.0, hi_f = 0.0, hi_h = 0.0;
-    double t = -1.0;
-    for (int r = 0; r < LS_ROUNDS; ++r) {
+    // phi'(t) = phi'(0) + sum_j D_j(t) + 2 gamma G(d) t, phi'(0) = g.d from the
+    // reduced gradient; thread 0 keeps the bracket [lo, hi] (phi'(lo) < 0 <
+    // phi'(hi)) and picks the trial points; all CTAs see the same sums.
+    const double cg1 = 2.0 * a.gamma * Gd;
+    double *s_ls_state = s_sc + 8;  // lo_t lo_f lo_h hi_t hi_f hi_h t done
+    if (tid == 0) {
+      s_ls_state[0] = 0.0; s_ls_state[1] = phi0; s_ls_state[2] = -1.0;
+      s_ls_state[3] = 1.0; s_ls_state[4] = 0.0; s_ls_state[5] = -1.0;
+      s_ls_state[6] = -1.0; s_ls_state[7] = phi0 < 0.0 ? 0.0 : 1.0;
+      if (!(phi0 < 0.0)) s_ls_state[6] = 0.0;  // not a descent direction
+    }
+    __syncthreads();
+    for (int r = 0; r < LS_ROUNDS && s_ls_state[7] == 0.0; ++r) {
       if (tid < LS_POINTS) {
+        const double lo_t = s_ls_state[0], lo_f = s_ls_state[1], lo_h = s_ls_state[2];
+        const double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
         double tq;
         if (r == 0) {
-          tq = (double)tid / (double)(LS_POINTS - 1);
+          tq = (double)(tid + 1) / (double)LS_POINTS;  // 1/16 .. 1
         } else {
           const double span = hi_t - lo_t;
           if (tid == 0) tq = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
@@ -435,38 +497,40 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         break;
       }
       ls_parity ^= 1;
-      // bracket update from the 16 points (identical in every CTA)
-      if (r == 0) {
-        const double f0 = s_res[0] + cg0;
-        const double f1 = s_res[LS_POINTS - 1] + cg0 + cg1;
-        if (!(f0 < 0.0)) { t = 0.0; break; }  // not a descent direction
-        if (f1 <= 0.0) { t = 1.0; break; }
-        lo_f = f0; lo_h = s_res[LS_POINTS] + cg1;
-        hi_f = f1; hi_h = s_res[2 * LS_POINTS - 1] + cg1;
+      if (tid == 0) {
+        double lo_t = s_ls_state[0], lo_f = s_ls_state[1], lo_h = s_ls_state[2];
+        double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
+        double t = -1.0;
+        for (int p = 0; p < LS_POINTS; ++p) {
+          const double tp = (double)s_t[p];
+          const double f = phi0 + s_res[p] + cg1 * tp, h = s_res[LS_POINTS + p] + cg1;
+          if (r == 0 && p == 0) lo_h = h;  // slope just right of 0 (first point's side pattern)
+          if (r == 0 && p == LS_POINTS - 1) {
+            if (f <= 0.0) { t = 1.0; break; }
+            if (hi_h < 0.0) { hi_f = f; hi_h = h; }
+          }
+          if (f == 0.0) { t = tp; break; }
+          if (f < 0.0 && tp > lo_t && tp < hi_t) { lo_t = tp; lo_f = f; lo_h = h; }
+          if (f > 0.0 && tp < hi_t && tp > lo_t) { hi_t = tp; hi_f = f; hi_h = h; }
+        }
+        if (t < 0.0) {
+          const double span = hi_t - lo_t;
+          const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
+          const double na = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
+          const double nb = hi_h > 0.0 ? hi_t - hi_f / hi_h : -2.0;
+          // both ends on one linear piece of phi' (their Newton steps agree): exact
+          if (!(span > 0.0) || fabs(na - nb) <= 1e-6 * fabs(tsec) || span <= 1e-7 * hi_t ||
+              r == LS_ROUNDS - 1)
+            t = tsec;
+        }
+        s_ls_state[0] = lo_t; s_ls_state[1] = lo_f; s_ls_state[2] = lo_h;
+        s_ls_state[3] = hi_t; s_ls_state[4] = hi_f; s_ls_state[5] = hi_h;
+        if (t >= 0.0) { s_ls_state[6] = fmin(fmax(t, lo_t), 1.0); s_ls_state[7] = 1.0; }
       }
-      bool exact = false;
-      for (int p = 0; p < LS_POINTS; ++p) {
-        const double tp = (double)s_t[p];
-        const double f = s_res[p] + cg0 + cg1 * tp, h = s_res[LS_POINTS + p] + cg1;
-        if (f == 0.0 && tp > 0.0) { t = tp; exact = true; break; }
-        if (f < 0.0 && tp > lo_t && tp < hi_t) { lo_t = tp; lo_f = f; lo_h = h; }
-        if (f > 0.0 && tp < hi_t && tp > lo_t) { hi_t = tp; hi_f = f; hi_h = h; }
-      }
-      if (exact) break;
-      const double span = hi_t - lo_t;
-      const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
-      const double na = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
-      const double nb = hi_h > 0.0 ? hi_t - hi_f / hi_h : -2.0;
-      // both ends on one linear piece of phi' (their Newton steps agree): exact
-      if (!(span > 0.0) || fabs(na - nb) <= 1e-6 * fabs(tsec) || span <= 1e-7 * hi_t) {
-        t = tsec;
-        break;
-      }
+      __syncthreads();
     }
     if (!alive) break;
-    if (t < 0.0) t = lo_t - lo_f * (hi_t - lo_t) / (hi_f - lo_f);
-    if (!(t >= lo_t)) t = lo_t;
-    t = fmin(t, 1.0);
+    const double t = s_ls_state[6] >= 0.0 ? s_ls_state[6] : s_ls_state[0];
     if (timer) { unsigned long long c1 = vmat_globaltimer(); tL += c1 - c0; c0 = c1; }
     if (t <= 0.0) { status = VMAT_ENOTCONV; break; }
 
@@ -498,12 +562,14 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
 #pragma unroll 4
-  for (int s = 0; s < ns; ++s) {
-    const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + base);
+  for (int q = 0; q < nnzs; ++q) {
+    const int s = s_nz[q], mk = s_mask[s];
+    const float *Ms = a.M + (size_t)s * a.Vpad;
     const float ys = s_yf[s];
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
-      const float4 q = __ldg(Ms + tid + nthr * m);
+      if (!(mk >> m & 1)) continue;
+      const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
       z[4 * m] = fmaf(q.x, ys, z[4 * m]);
       z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
       z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
@@ -521,7 +587,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       zo[q] = z[v];
       cst += vmat_F((double)z[v], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
     }
-    const size_t off = base + 4 * (tid + (size_t)nthr * m);
+    const size_t off = SUB_OFF(m) + 4 * tid;
     *(float4 *)(a.z_out + off) = make_float4(zo[0], zo[1], zo[2], zo[3]);
     *(float4 *)(a.fp_out + off) = make_float4(fo[0], fo[1], fo[2], fo[3]);
   }
@@ -544,7 +610,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       for (int q = lane; q < (int)gridDim.x; q += 32)
         c += __ldcg(a.part + (size_t)q * stride + COST_OFF(N));
       c = warp_sum(c);
-      const double G = G_warp(s_y, a.theta, N, a.cyclic);
+      const double G = G_inv(s_y, s_igr, N);
       if (lane == 0) {
         a.out->cost_active = c;
         a.out->smooth = G;
@@ -573,9 +639,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 
 // ---------------------------------------------------------------- launch
 static size_t master_smem_bytes(int N, int nthr, int vpt) {
-  const size_t tile = (size_t)nthr * vpt;
-  return (size_t)(5 * N + 32 + 32 + 16 * 32) * 8 +
-         (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + tile * 4 + (size_t)(8 + N) * 4 + 16;
+  const size_t tile = (size_t)nthr * vpt, ng = vpt / 4;
+  return (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +
+         (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + tile * 4 + (size_t)N * ng * 4 +
+         (size_t)(8 + 4 * N + 1 + N * ng) * 4 + 16;
 }
 
 template <int VPT>
@@ -623,6 +690,7 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
                                int32_t *rec_iters, int32_t *rec_status) {
   MasterArgs a;
   a.M = ctx->M;
+  a.tflag = ctx->tflag;
   a.Vpad = ctx->Vpad;
   a.nslots = ctx->n_slots;
   a.N = ctx->N;

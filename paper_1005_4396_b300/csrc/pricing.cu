@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
                                                   const SelRec *__restrict__ sel,
                                                   const int16_t *__restrict__ sl,
                                                   const int16_t *__restrict__ sr,
-                                                  float *__restrict__ Mcol) {
+                                                  float *__restrict__ Mcol, int tile,
+                                                  int32_t *__restrict__ tflag) {
   __shared__ int16_t L[VMAT_MAX_ROWS], Rr[VMAT_MAX_ROWS];
   __shared__ int sk;
   if (threadIdx.x == 0) sk = sel->status == 0 ? sel->k : -1;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
   const int k = sk;
   if (a >= Va || k < 0) {
     Mcol[a] = 0.f;
-    return;
+    return;  // padding and failed selections leave the tile flags alone
   }
   const int32_t RC = R * C, lo = k * RC, hi = lo + RC;
   int64_t b = ptr[a], e = ptr[a + 1];
@@ -251,12 +252,27 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
     }
   }
   Mcol[a] = acc;
+  // mark the master subtile holding voxel a as nonzero for this column
+  // (subtiles are whole multiples of 128 voxels: a warp never straddles two)
+  if (__any_sync(__activemask(), acc != 0.f) && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
+    atomicOr(tflag + a / tile, 1);
 }
 
 // commit the selected aperture as plan column `slot`
 __global__ void k_commit(const SelRec *sel, const int16_t *sl, const int16_t *sr, int R, int slot,
                          uint8_t *occ, int16_t *lleaf, int16_t *rleaf, int32_t *slot_beam,
-                         double *y, int *dstatus) {
+                         double *y, int *dstatus, const int32_t *tf, int nsub,
+                         int32_t *rec_subtiles) {
+  if (rec_subtiles) {  // nonzero subtiles of the new column
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int q = threadIdx.x; q < nsub; q += blockDim.x) c += tf[q] != 0;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *rec_subtiles = cnt;
+  }
   const int k = sel->status == 0 ? sel->k : -1;
   if (k < 0) {
     if (threadIdx.x == 0) atomicCAS(dstatus, 0, (int)VMAT_ESTATE);
@@ -273,14 +289,18 @@ __global__ void k_commit(const SelRec *sel, const int16_t *sl, const int16_t *sr
   }
 }
 
-vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot) {
+vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot, int32_t *rec_subtiles) {
   cudaStream_t st = ctx->stream;
   float *Mcol = ctx->M + (size_t)slot * ctx->Vpad;
+  const int nsub = ctx->master_grid * (ctx->master_vpt / 4);
+  int32_t *tf = ctx->tflag + (size_t)slot * nsub;
+  const int tile = ctx->master_block * 4;  // master subtile
+  VMAT_CUDA(ctx, cudaMemsetAsync(tf, 0, (size_t)nsub * 4, st));
   unsigned nb = (unsigned)((ctx->Vpad + 255) / 256);
   int us = ctx->dt != VMAT_F32;
 #define VMAT_AP_ARGS                                                                              \
   ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, ctx->Va, ctx->Vpad, ctx->R, \
-      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol
+      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol, tile, tf
   if (ctx->dt == VMAT_F32) {
     typedef float TV;
     k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);
@@ -293,7 +313,8 @@ vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot) {
   }
 #undef VMAT_AP_ARGS
   k_commit<<<1, 128, 0, st>>>(ctx->sel, ctx->sel_l, ctx->sel_r, ctx->R, slot, ctx->occ, ctx->lleaf,
-                              ctx->rleaf, ctx->slot_beam, ctx->y, ctx->dstatus);
+                              ctx->rleaf, ctx->slot_beam, ctx->y, ctx->dstatus, tf, nsub,
+                              rec_subtiles);
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 2;
   return VMAT_OK;

@@ -377,6 +377,7 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   // plan state and workspaces
   const int N = ctx->N, R = ctx->R;
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->M, (size_t)N * Vpad));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->tflag, (size_t)N * ctx->master_grid * (ctx->master_vpt / 4)));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->occ, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->lleaf, (size_t)N * R));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->rleaf, (size_t)N * R));
@@ -439,7 +440,7 @@ extern "C" void vmat_destroy(vmat_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->fa32, ctx->act_vox, ctx->vox2act, ctx->sid_full, ctx->sid, ctx->tabf, ctx->tabd,
                   ctx->theta, ctx->scale, ctx->bm_ptr, ctx->bm_col, ctx->bm_val, ctx->vm_ptr,
-                  ctx->vm_col, ctx->vm_val, ctx->M, ctx->occ, ctx->lleaf, ctx->rleaf,
+                  ctx->vm_col, ctx->vm_val, ctx->M, ctx->tflag, ctx->occ, ctx->lleaf, ctx->rleaf,
                   ctx->slot_beam, ctx->y, ctx->zact, ctx->fpact, ctx->rho_plan, ctx->g,
                   ctx->fgather, ctx->xs, ctx->ap_price, ctx->ap_l, ctx->ap_r, ctx->sel, ctx->sel_l,
                   ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats};
@@ -471,6 +472,8 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
   for (int q = 0; q < 4; ++q) out->master_ms[q] = ms[q] * 1e-6;
   out->master_syncs = (int64_t)ms[4];
   out->master_pg_iters = (int64_t)ms[5];
+  out->subtile_voxels = ctx->master_block * 4;
+  out->n_subtiles = ctx->master_grid * (ctx->master_vpt / 4);
   return VMAT_OK;
 }
 
@@ -488,6 +491,7 @@ extern "C" vmat_status vmat_reset(vmat_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   const int N = ctx->N, R = ctx->R;
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->occ, 0, N, st));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->tflag, 0, (size_t)N * ctx->master_grid * (ctx->master_vpt / 4) * 4, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->lleaf, 0, (size_t)N * R * 2, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->rleaf, 0, (size_t)N * R * 2, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->slot_beam, 0xff, (size_t)N * 4, st));

@@ -320,12 +320,15 @@ __global__ void __launch_bounds__(256) k_price32(const int64_t *__restrict__ ptr
                                                  const TV *__restrict__ val,
                                                  const float *__restrict__ scale, int use_scale,
                                                  const float *__restrict__ Fa, int64_t B,
+                                                 const float *__restrict__ colw,
                                                  float *__restrict__ G) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
   if (i >= B) return;
   float acc = warp_row_dot32<TV>(col, val, Fa, nullptr, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
-  G[(size_t)i * 32 + lane] = use_scale ? acc * scale[i] : acc;
+  if (use_scale) acc *= scale[i];
+  if (colw) acc *= colw[lane];
+  G[(size_t)i * 32 + lane] = acc;
 }
 
 __global__ void k_gather_active32(const float *__restrict__ full, const int32_t *__restrict__ act,
@@ -365,7 +368,7 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
   return VMAT_OK;
 }
 
-vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G) {
+vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const float *colw, float *G) {
   cudaStream_t st = ctx->stream;
   if (!ctx->fa32) VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fa32, (size_t)(ctx->Va > 0 ? ctx->Va : 1) * 32));
   float *Fa = ctx->fa32;
@@ -375,14 +378,14 @@ vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G) 
   int us = ctx->dt != VMAT_F32;
   if (ctx->dt == VMAT_F32)
     k_price32<float><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
-                                         ctx->scale, us, Fa, ctx->B, G);
+                                         ctx->scale, us, Fa, ctx->B, colw, G);
   else if (ctx->dt == VMAT_F16)
     k_price32<__half><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const __half *)ctx->bm_val,
-                                          ctx->scale, us, Fa, ctx->B, G);
+                                          ctx->scale, us, Fa, ctx->B, colw, G);
   else
     k_price32<__nv_bfloat16><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col,
                                                  (const __nv_bfloat16 *)ctx->bm_val, ctx->scale,
-                                                 us, Fa, ctx->B, G);
+                                                 us, Fa, ctx->B, colw, G);
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 2;
   return VMAT_OK;

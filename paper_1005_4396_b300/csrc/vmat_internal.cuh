@@ -62,6 +62,7 @@ struct vmat_ctx {
 
   // plan state
   float *M = nullptr;          // [N][Vpad] aperture-dose columns in order of addition
+  int32_t *tflag = nullptr;    // [N][master_grid*vpt/4] 1 if column s is nonzero in master subtile
   uint8_t *occ = nullptr;      // [N]
   int16_t *lleaf = nullptr, *rleaf = nullptr;  // [N*R]
   int32_t *slot_beam = nullptr;                // [N]
@@ -143,12 +144,12 @@ vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act);
 vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float *fp_full,
                              double *cost_dev);
 vmat_status vmat_launch_pricing(vmat_ctx *ctx, const float *g);
-vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot);
+vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot, int32_t *rec_subtiles = nullptr);
 vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, double rho_ref,
                                int set_rho_plan, double *rec_cost, double *rec_rho,
                                int32_t *rec_iters, int32_t *rec_status);
 vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, float *Fp,
                                      double *cost_dev);
-vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, float *G);
+vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const float *colw, float *G);
 vmat_status vmat_configure_master(vmat_ctx *ctx);
 int64_t vmat_master_scratch(int grid, int N);

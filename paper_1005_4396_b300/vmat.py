@@ -49,7 +49,8 @@ class vmat_info(ctypes.Structure):
                 ("n_cols", _i32), ("n_beamlets", _i64), ("nnz", _i64), ("n_columns", _i32),
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
                 ("master_block", _i32), ("n_launches", _i64), ("master_ms", _d * 4),
-                ("master_syncs", _i64), ("master_pg_iters", _i64)]
+                ("master_syncs", _i64), ("master_pg_iters", _i64), ("subtile_voxels", _i32),
+                ("n_subtiles", _i32)]
 
 
 class vmat_column(ctypes.Structure):
@@ -64,7 +65,7 @@ class vmat_colgen_opts(ctypes.Structure):
 class vmat_colgen_result(ctypes.Structure):
     _fields_ = [("angle_order", _p), ("l", _p), ("r", _p), ("y", _p), ("price", _p),
                 ("runner_up", _p), ("cost", _p), ("kkt", _p), ("master_iters", _p),
-                ("phase_ms", _p)]
+                ("phase_ms", _p), ("col_subtiles", _p)]
 
 
 EXPORTS = {
@@ -81,10 +82,13 @@ EXPORTS = {
     "vmat_reset": [_p],
     "vmat_colgen_run": [_p, ctypes.POINTER(vmat_colgen_opts), ctypes.POINTER(vmat_colgen_result)],
     "vmat_dose_batch32": [_p, _p, _p, _p, _p],
-    "vmat_price_batch32": [_p, _p, _p],
+    "vmat_price_batch32": [_p, _p, _p, _p],
     "vmat_selftest_grid_wait": [_p, _i32, _d],
     "vmat_set_profiling": [_p, _i32],
     "vmat_dose_cost_noalloc": [_i32, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p, _p],
+    "vmat_aperture_fluence_batch32": [_p, _p, _p, _p, _p],
+    "vmat_aperture_adjoint_batch32": [_p, _p, _p, _p, _p, _p, _p],
+    "vmat_smoothing_batch32": [_p, _p, _p, _p],
 }
 
 _lib = None
@@ -237,16 +241,16 @@ def vmat_colgen_run(ctx, N, R, n_iters, master_max_iters=100000, kkt_tol=1e-6, f
     out = dict(k=np.zeros(n, np.int32), lleaf=np.zeros(N * R, np.int16),
                rleaf=np.zeros(N * R, np.int16), y=np.zeros(N), p=np.zeros(n), p2=np.zeros(n),
                cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32),
-               phase_ms=np.zeros((n, 4)))
+               phase_ms=np.zeros((n, 4)), col_subtiles=np.zeros(n, np.int32))
     res = vmat_colgen_result(*[out[k].ctypes.data for k in
                                ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters",
-                                "phase_ms")])
+                                "phase_ms", "col_subtiles")])
     st = load_library().vmat_colgen_run(ctx, ctypes.byref(opts), ctypes.byref(res))
     out["status"] = st
     if st != VMAT_OK and not (allow_notconv and st == VMAT_ENOTCONV):
         _check(ctx, st)
     if n_iters == 0:
-        for k in ("k", "p", "p2", "cost", "rho", "iters", "phase_ms"):
+        for k in ("k", "p", "p2", "cost", "rho", "iters", "phase_ms", "col_subtiles"):
             out[k] = out[k][:0]
     return out
 
@@ -258,8 +262,8 @@ def vmat_dose_batch32(ctx, X, Z, fprime=None, want_cost=True):
     return np.array(c[:]) if want_cost else None
 
 
-def vmat_price_batch32(ctx, Fp, G):
-    _check(ctx, load_library().vmat_price_batch32(ctx, _ptr(Fp), _ptr(G)))
+def vmat_price_batch32(ctx, Fp, G, w=None):
+    _check(ctx, load_library().vmat_price_batch32(ctx, _ptr(Fp), _ptr(w), _ptr(G)))
 
 
 def vmat_dose_cost_noalloc(n_vox, row_ptr, beamlet, val, x, struct_id, params, n_struct,
@@ -271,6 +275,21 @@ def vmat_dose_cost_noalloc(n_vox, row_ptr, beamlet, val, x, struct_id, params, n
         _ptr(params), int(n_struct), _ptr(z), _ptr(fprime), _ptr(cost), stream)
     if st != VMAT_OK:
         raise VmatError(st, load_library().vmat_last_error(None).decode())
+
+
+def vmat_aperture_fluence_batch32(ctx, l, r, Y, X):
+    _check(ctx, load_library().vmat_aperture_fluence_batch32(ctx, _ptr(l), _ptr(r), _ptr(Y), _ptr(X)))
+
+
+def vmat_aperture_adjoint_batch32(ctx, l, r, GX, GY, Y=None, w=None):
+    _check(ctx, load_library().vmat_aperture_adjoint_batch32(ctx, _ptr(l), _ptr(r), _ptr(GX),
+                                                             _ptr(Y), _ptr(w), _ptr(GY)))
+
+
+def vmat_smoothing_batch32(ctx, Y, dG=None):
+    g = (ctypes.c_double * 32)()
+    _check(ctx, load_library().vmat_smoothing_batch32(ctx, _ptr(Y), g, _ptr(dG)))
+    return np.array(g[:])
 
 
 def vmat_set_profiling(ctx, on):
@@ -376,9 +395,9 @@ class Plan:
         cost = vmat_dose_batch32(self.ctx, X, Z, Fp)
         return Z, Fp, cost
 
-    def price_batch32(self, Fp):
+    def price_batch32(self, Fp, w=None):
         import torch
         _require_cuda(Fp, torch.float32, self.prob.n_vox * 32, "Fp")
         G = self._t(self.cfg.n_beamlets * 32)
-        vmat_price_batch32(self.ctx, Fp, G)
+        vmat_price_batch32(self.ctx, Fp, G, w)
         return G
