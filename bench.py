@@ -393,6 +393,71 @@ def run_cpu_baseline(prob, args):
                       f"fewest columns, so this overstates the oracle's whole-plan rate"}
 
 
+# ---------------------------------------------------------------- batched plans
+def run_batched(args):
+    """Sixteen independent plans of uneven size (seeds 10-25: 90-180 beams,
+    40x40 or 60x40 MLC, prostate- or head-and-neck-like, 0.4-2.2 M voxels):
+    FP16-D plans in one tuned batch (lanes of concurrent plans, one CUDA graph
+    launch) against the plain FP32 single-plan loop on the same GPU."""
+    import torch
+    from paper_1005_4396_b300 import inputs, vmat
+    torch.cuda.set_device(0)
+    cfgs = inputs.batch_configs(scale=args.batch_scale)
+    kkt = 1e-6
+    plans16, probs, fp32 = [], [], []
+    t_setup = time.perf_counter()
+    for c in cfgs:
+        prob = inputs.make_problem(c)
+        # plain FP32 single-plan loop: whole plan on the whole GPU
+        with vmat.Plan(prob, val_f32=True) as p32:
+            p32.colgen_run(kkt_tol=kkt)  # warm-up
+            p32.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r32 = p32.colgen_run(kkt_tol=kkt)
+            b.record()
+            torch.cuda.synchronize()
+            fp32.append(a.elapsed_time(b) / 1e3)
+        p16 = vmat.Plan(prob, dtype="f16", val_f32=True)
+        plans16.append(p16)
+        probs.append(prob if len(probs) < 3 else None)  # keep a few for the dose check
+        del prob
+    t_setup = time.perf_counter() - t_setup
+    batch = vmat.Batch(plans16)
+    lanes, trial = batch.tune(trial_iters=20, kkt_tol=kkt)
+    batch.run(kkt_tol=kkt)  # warm-up replay
+    outs, plan_ms, total_ms = batch.run(kkt_tol=kkt)
+    errs = []
+    import oracle
+    for prob, plan, out in zip(probs, plans16, outs):
+        if prob is None:
+            continue
+        z = plan.plan_dose().cpu().numpy()
+        x = oracle.aperture_fluence(prob.cfg, out["lleaf"], out["rleaf"], out["y"])
+        z64 = oracle.dose(prob, x)
+        errs.append(float(np.abs(z - z64).max() / prob.T.max() * 100))
+    n = len(plans16)
+    iters = sum(c.n_angles for c in cfgs)
+    out = {"metric": "plans/s (FP16-D batched, one graph launch) vs FP32 single-plan loop",
+           "value": round(n / (total_ms / 1e3), 4), "unit": "plans/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f16-D, f32 accumulate", "data": "synthetic",
+           "config": {"workload": f"{n} plans, seeds 10-25, grid voxels "
+                                  f"{min(c.n_vox for c in cfgs)}-{max(c.n_vox for c in cfgs)}, "
+                                  f"beams 90-180, MLC 40x40/60x40, scale {args.batch_scale}",
+                      "lanes": lanes, "tuner_trial_ms": trial},
+           "batched_s": round(total_ms / 1e3, 3),
+           "per_plan_wall_s": [round(v / 1e3, 3) for v in plan_ms],
+           "fp32_single_plan_loop": {"plans_per_s": round(n / sum(fp32), 4),
+                                     "per_plan_s": [round(v, 3) for v in fp32]},
+           "cg_iters_per_s_batched": round(iters / (total_ms / 1e3), 2),
+           "max_dose_err_pct_rx_sampled": errs,
+           "setup_s": round(t_setup, 1)}
+    batch.close()
+    for p in plans16:
+        p.close()
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- profiling cases
 def run_case(args):
     """Small cases sized for an ncu capture (a few GB on the device, inputs
@@ -470,9 +535,15 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--case", default=None, choices=["master", "spmv"],
                     help="small case for an ncu capture instead of the benchmark")
+    ap.add_argument("--batched", action="store_true",
+                    help="the sixteen-plan batch (FP16-D, graph) against the FP32 single-plan loop")
+    ap.add_argument("--batch-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.case:
         run_case(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -247,6 +247,41 @@ VMAT_API vmat_status vmat_aperture_adjoint_batch32(vmat_ctx *ctx, const int16_t 
 VMAT_API vmat_status vmat_smoothing_batch32(vmat_ctx *ctx, const float *Y_dev, double *G_host,
                                             float *dG_dev);
 
+/* Master-kernel CTA budget of a plan: tile its persistent master kernel for
+ * at most max_ctas co-resident CTAs (0: every SM).  Used to run several plans'
+ * master kernels side by side on disjoint SMs.  The plan must have no
+ * columns (call vmat_reset first); re-allocates the aperture-dose matrix. */
+VMAT_API vmat_status vmat_set_master_budget(vmat_ctx *ctx, int32_t max_ctas);
+
+/* ---- many independent plans (planning throughput; not in the paper) ----
+ * A batch groups existing contexts (not owned) into "lanes": each lane is a
+ * stream that runs its plans one after another, and every plan's master
+ * kernel is tiled for SMs/lanes CTAs so that lanes co-run.  The whole
+ * multi-lane run (reset + all iterations of every plan) is captured once
+ * into a CUDA graph and replayed with one launch.  While a plan belongs to a
+ * batch its context runs on the batch's lane stream. */
+typedef struct vmat_batch vmat_batch;
+VMAT_API vmat_status vmat_batch_create(vmat_ctx *const *plans, int32_t n_plans, void *cuda_stream,
+                                       vmat_batch **out);
+VMAT_API void vmat_batch_destroy(vmat_batch *b);
+VMAT_API const char *vmat_batch_last_error(const vmat_batch *b);
+/* Use `lanes` concurrent lanes (1..min(plans, SMs)); plans are dealt to the
+ * lane with the least estimated work (active voxels x beams), largest first.
+ * VMAT_EINVAL if some plan's active voxels do not fit SMs/lanes CTAs. */
+VMAT_API vmat_status vmat_batch_configure(vmat_batch *b, int32_t lanes);
+/* Autotuner: times a captured trial run of the first trial_iters iterations
+ * of every plan for 1, 2, 4 and 8 lanes (ms_out [4], -1 where infeasible) and
+ * configures the fastest (lanes_out). */
+VMAT_API vmat_status vmat_batch_tune(vmat_batch *b, int32_t trial_iters, int32_t master_max_iters,
+                                     double kkt_tol, int32_t *lanes_out, double *ms_out);
+/* Run every plan's full column generation (one aperture per beam) from an
+ * empty plan as one graph launch.  res [n_plans] as for vmat_colgen_run
+ * (phase_ms unused), plan_ms [n_plans] time from the launch to each plan's
+ * end, total_ms the whole launch (either may be NULL). */
+VMAT_API vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_iters, double kkt_tol,
+                                           vmat_colgen_result *res, double *plan_ms,
+                                           double *total_ms);
+
 /* Dose and voxel cost without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not let a
  * library allocate GPU memory (a host framework that owns a fixed device pool

@@ -142,10 +142,22 @@ extern "C" vmat_status vmat_plan_dose(vmat_ctx *ctx, float *z_dev) {
 }
 
 // ---------------------------------------------------------------- column generation
-struct Records {
-  int32_t *k, *iters, *status, *tiles;
-  double *p, *p2, *cost, *rho;
-};
+vmat_status vmat_enqueue_colgen(vmat_ctx *ctx, int n, int master_max_iters, double kkt_tol,
+                                const Records &rec, bool fresh) {
+  for (int t = 0; t < n; ++t) {
+    vmat_status s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g);
+    if (s != VMAT_OK) return s;
+    s = vmat_launch_pricing_rec(ctx, ctx->g, rec.k + t, rec.p + t, rec.p2 + t);
+    if (s != VMAT_OK) return s;
+    s = vmat_launch_add_column(ctx, ctx->n_slots, rec.tiles + t);
+    if (s != VMAT_OK) return s;
+    ctx->n_slots += 1;
+    s = vmat_launch_master(ctx, master_max_iters, kkt_tol, 0.0, fresh && t == 0 ? 1 : 0,
+                           rec.cost + t, rec.rho + t, rec.iters + t, rec.status + t);
+    if (s != VMAT_OK) return s;
+  }
+  return VMAT_OK;
+}
 
 extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
                                        vmat_colgen_result *res) {

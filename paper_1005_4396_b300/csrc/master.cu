@@ -655,10 +655,11 @@ static cudaError_t master_occupancy(int nthr, size_t smem, int *nb) {
 
 vmat_status vmat_configure_master(vmat_ctx *ctx) {
   const int64_t Va = ctx->Va > 0 ? ctx->Va : 1;
+  const int sms = ctx->sm_budget > 0 && ctx->sm_budget < ctx->num_sms ? ctx->sm_budget : ctx->num_sms;
   int vpt = 4, nthr = 0;
   for (vpt = 4; vpt <= 32; vpt *= 2) {
     int64_t threads = (Va + vpt - 1) / vpt;
-    int64_t per_sm = (threads + ctx->num_sms - 1) / ctx->num_sms;
+    int64_t per_sm = (threads + sms - 1) / sms;
     nthr = (int)(((per_sm + 31) / 32) * 32);
     if (nthr < 64) nthr = 64;
     if (nthr <= 512) break;
@@ -734,7 +735,17 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   // set it for this context's launch (another context may have lowered it)
   VMAT_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)ctx->master_smem));
-  VMAT_CUDA(ctx, cudaLaunchCooperativeKernel(fn, grid, block, args, ctx->master_smem, ctx->stream));
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = block;
+  lc.dynamicSmemBytes = ctx->master_smem;
+  lc.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident (the grid waits on itself)
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  VMAT_CUDA(ctx, cudaLaunchKernelExC(&lc, fn, args));
   ctx->n_launches += 1;
   return VMAT_OK;
 }

@@ -264,6 +264,66 @@ static vmat_status build_storage(vmat_ctx *ctx, Tmp &tmp, const int32_t *colv, c
   return VMAT_OK;
 }
 
+// Buffers whose size follows the master kernel's tiling (padded voxel count,
+// grid): structure ids of the active voxels, the aperture-dose matrix and its
+// subtile flags, plan dose and derivative, reduction scratch.
+static vmat_status alloc_tiled(vmat_ctx *ctx) {
+  cudaStream_t st = ctx->stream;
+  const int32_t Vpad = ctx->Vpad;
+  const int N = ctx->N;
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sid, Vpad));
+  k_active_sid<<<(Vpad + 255) / 256, 256, 0, st>>>(ctx->sid_full, ctx->act_vox, ctx->Va, Vpad, ctx->sid);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->M, (size_t)N * Vpad));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->M, 0, (size_t)N * Vpad * 4, st));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->tflag, (size_t)N * ctx->master_grid * (ctx->master_vpt / 4)));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->zact, Vpad));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fpact, Vpad));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fgather, Vpad));
+  // scratch: master partials [grid][N+extra] + reduced gradient [N]; dose
+  // partials [ceil(Va/8)] and batched [ceil(Va/8)][32]; result slots at the end
+  int64_t nbv = ((int64_t)ctx->Va + 7) / 8 + 1;
+  int64_t need = vmat_master_scratch(ctx->master_grid, N);
+  if (nbv * 32 > need) need = nbv * 32;
+  ctx->red_len = need + 128;
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->red, ctx->red_len));
+  return VMAT_OK;
+}
+
+static void free_tiled(vmat_ctx *ctx) {
+  void **ptrs[] = {(void **)&ctx->sid, (void **)&ctx->M, (void **)&ctx->tflag, (void **)&ctx->zact,
+                   (void **)&ctx->fpact, (void **)&ctx->fgather, (void **)&ctx->red};
+  size_t bytes[] = {(size_t)ctx->Vpad, (size_t)ctx->N * ctx->Vpad * 4,
+                    (size_t)ctx->N * ctx->master_grid * (ctx->master_vpt / 4) * 4,
+                    (size_t)ctx->Vpad * 4, (size_t)ctx->Vpad * 4, (size_t)ctx->Vpad * 4,
+                    (size_t)ctx->red_len * 8};
+  for (int q = 0; q < 7; ++q)
+    if (*ptrs[q]) {
+      cudaFree(*ptrs[q]);
+      *ptrs[q] = nullptr;
+      ctx->device_bytes -= (int64_t)bytes[q];
+    }
+}
+
+extern "C" vmat_status vmat_set_master_budget(vmat_ctx *ctx, int32_t max_ctas) {
+  if (!ctx) return VMAT_EINVAL;
+  if (max_ctas < 0) return vmat_fail(ctx, VMAT_EINVAL, "max_ctas must be >= 0");
+  if (ctx->n_slots != 0) return vmat_fail(ctx, VMAT_EINVAL, "the plan has columns: call vmat_reset first");
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int old_budget = ctx->sm_budget;
+  ctx->sm_budget = max_ctas;
+  vmat_status s = vmat_configure_master(ctx);
+  if (s != VMAT_OK) {
+    ctx->sm_budget = old_budget;
+    vmat_configure_master(ctx);
+    return s;
+  }
+  free_tiled(ctx);
+  s = alloc_tiled(ctx);
+  if (s != VMAT_OK) return s;
+  return vmat_reset(ctx);
+}
+
 static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_t st,
                                vmat_ctx *ctx) {
   Tmp tmp;
@@ -361,9 +421,6 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   // master launch shape fixes the padded voxel count
   vmat_status s3 = vmat_configure_master(ctx);
   if (s3 != VMAT_OK) return s3;
-  const int32_t Vpad = ctx->Vpad;
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sid, Vpad));
-  k_active_sid<<<(Vpad + 255) / 256, 256, 0, st>>>(ctx->sid_full, ctx->act_vox, ctx->Va, Vpad, ctx->sid);
 
   // constant cost of the voxels D never reaches
   double *part, *sum;
@@ -376,18 +433,13 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
 
   // plan state and workspaces
   const int N = ctx->N, R = ctx->R;
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->M, (size_t)N * Vpad));
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->tflag, (size_t)N * ctx->master_grid * (ctx->master_vpt / 4)));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->occ, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->lleaf, (size_t)N * R));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->rleaf, (size_t)N * R));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->slot_beam, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->y, N));
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->zact, Vpad));
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fpact, Vpad));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->rho_plan, 1));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->g, B));
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fgather, Vpad));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->xs, B));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->ap_price, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->ap_l, (size_t)N * R));
@@ -395,15 +447,6 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sel, 1));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sel_l, R));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sel_r, R));
-  {
-    // scratch: master partials [grid][N+16] + reduced gradient [N]; dose
-    // partials [ceil(Va/8)] and batched [ceil(Va/8)][32]; 64 result slots at the end
-    int64_t nbv = ((int64_t)ctx->Va + 7) / 8 + 1;
-    int64_t need = vmat_master_scratch(ctx->master_grid, N);
-    if (nbv * 32 > need) need = nbv * 32;
-    ctx->red_len = need + 128;
-  }
-  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->red, ctx->red_len));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->mout, 1));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->bar, 2));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->mstats, 8));
@@ -411,7 +454,8 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->dstatus, 1));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->dstatus, 0, 4, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, st));
-  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->M, 0, (size_t)N * Vpad * 4, st));
+  vmat_status s4 = alloc_tiled(ctx);
+  if (s4 != VMAT_OK) return s4;
   VMAT_CUDA(ctx, cudaStreamSynchronize(st));
   return vmat_reset(ctx);
 }
@@ -486,8 +530,9 @@ __global__ void k_init_fprime(const uint8_t *sid, const float *tab, int32_t Vpad
   fp[a] = vmat_dF(0.f, tab[q], tab[256 + q], tab[512 + q]);
 }
 
-extern "C" vmat_status vmat_reset(vmat_ctx *ctx) {
-  if (!ctx) return VMAT_EINVAL;
+// Clear the plan state on the context's stream without waiting (usable while
+// the stream is being captured into a graph).
+vmat_status vmat_enqueue_reset(vmat_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   const int N = ctx->N, R = ctx->R;
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->occ, 0, N, st));
@@ -502,7 +547,15 @@ extern "C" vmat_status vmat_reset(vmat_ctx *ctx) {
                                                           ctx->fpact);
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 1;
-  VMAT_CUDA(ctx, cudaStreamSynchronize(st));
   ctx->n_slots = 0;
   return VMAT_OK;
 }
+
+extern "C" vmat_status vmat_reset(vmat_ctx *ctx) {
+  if (!ctx) return VMAT_EINVAL;
+  vmat_status s = vmat_enqueue_reset(ctx);
+  if (s != VMAT_OK) return s;
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return VMAT_OK;
+}
+

@@ -94,6 +94,7 @@ struct vmat_ctx {
   int64_t device_bytes = 0;
   int64_t n_launches = 0;      // kernels launched by this context
   int profiling = 0;
+  int sm_budget = 0;           // master kernel CTA budget (0: every SM)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -153,3 +154,14 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
 vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const float *colw, float *G);
 vmat_status vmat_configure_master(vmat_ctx *ctx);
 int64_t vmat_master_scratch(int grid, int N);
+vmat_status vmat_enqueue_reset(vmat_ctx *ctx);
+
+// Device-resident per-iteration records of a column-generation run.
+struct Records {
+  int32_t *k, *iters, *status, *tiles;
+  double *p, *p2, *cost, *rho;
+};
+// Enqueue n column-generation iterations on ctx->stream without any host
+// synchronisation or allocation (safe inside a stream capture).
+vmat_status vmat_enqueue_colgen(vmat_ctx *ctx, int n, int master_max_iters, double kkt_tol,
+                                const Records &rec, bool fresh);

@@ -155,6 +155,31 @@ def small_config(nx=20, ny=18, nz=6, n_angles=12, n_rows=6, n_cols=8, **kw) -> P
 CONFIGS = {"tiny": tiny_config, "prostate": prostate_config, "headneck": headneck_config}
 
 
+def batch_configs(seeds=range(10, 26), scale=1.0):
+    """Independent plans of uneven size, one per seed: beams N in {90, 120,
+    150, 180}, MLC 40x40 or 60x40, prostate- or head-and-neck-like
+    structures, grid voxel count V_target in [200k, 2.4M] (x scale) reached by
+    changing the voxel pitch over the same field of view."""
+    out = []
+    for seed in seeds:
+        u = rng.uniform(seed, 4)
+        N = (90, 120, 150, 180)[int(u[0] * 4)]
+        rows = 40 if u[1] < 0.5 else 60
+        hn = u[2] >= 0.5
+        vt = (200e3 + u[3] * (2.4e6 - 200e3)) * scale
+        base = headneck_config() if hn else prostate_config()
+        v0 = base.nx * base.ny * base.nz
+        f = (vt / v0) ** (1.0 / 3.0)
+        nx, ny, nz = (max(8, int(round(base.nx * f))), max(8, int(round(base.ny * f))),
+                      max(4, int(round(base.nz * f))))
+        h = base.h * base.nx / nx
+        w_row = base.w_row * base.n_rows / rows if not hn else base.w_row
+        out.append(dataclasses.replace(
+            base, name=f"plan{seed}{'-hn' if hn else '-pr'}", nx=nx, ny=ny, nz=nz, h=h,
+            n_angles=N, n_rows=rows, w_row=w_row, seed=seed))
+    return out
+
+
 # --------------------------------------------------------------------------
 # problem
 # --------------------------------------------------------------------------

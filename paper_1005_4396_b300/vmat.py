@@ -89,6 +89,13 @@ EXPORTS = {
     "vmat_aperture_fluence_batch32": [_p, _p, _p, _p, _p],
     "vmat_aperture_adjoint_batch32": [_p, _p, _p, _p, _p, _p, _p],
     "vmat_smoothing_batch32": [_p, _p, _p, _p],
+    "vmat_set_master_budget": [_p, _i32],
+    "vmat_batch_create": [_p, _i32, _p, ctypes.POINTER(_p)],
+    "vmat_batch_destroy": [_p],
+    "vmat_batch_last_error": [_p],
+    "vmat_batch_configure": [_p, _i32],
+    "vmat_batch_tune": [_p, _i32, _i32, _d, _p, _p],
+    "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
 }
 
 _lib = None
@@ -104,8 +111,8 @@ def load_library(path: str = LIB_PATH):
         for name, args in EXPORTS.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name == "vmat_destroy" else (
-                ctypes.c_char_p if name == "vmat_last_error" else ctypes.c_int)
+            f.restype = None if name in ("vmat_destroy", "vmat_batch_destroy") else (
+                ctypes.c_char_p if name in ("vmat_last_error", "vmat_batch_last_error") else ctypes.c_int)
         _lib = L
     return _lib
 
@@ -401,3 +408,77 @@ class Plan:
         G = self._t(self.cfg.n_beamlets * 32)
         vmat_price_batch32(self.ctx, Fp, G, w)
         return G
+
+
+def vmat_set_master_budget(ctx, max_ctas):
+    _check(ctx, load_library().vmat_set_master_budget(ctx, int(max_ctas)))
+
+
+def _result_arrays(N, R, n):
+    out = dict(k=np.zeros(n, np.int32), lleaf=np.zeros(N * R, np.int16),
+               rleaf=np.zeros(N * R, np.int16), y=np.zeros(N), p=np.zeros(n), p2=np.zeros(n),
+               cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32),
+               phase_ms=np.zeros((n, 4)), col_subtiles=np.zeros(n, np.int32))
+    res = vmat_colgen_result(*[out[k].ctypes.data for k in
+                               ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters",
+                                "phase_ms", "col_subtiles")])
+    return out, res
+
+
+class Batch:
+    """Many plans at once: lanes of concurrent plans, one CUDA graph per run.
+    While a Plan is in a batch its context runs on the batch's lane stream."""
+
+    def __init__(self, plans):
+        import torch
+        self.plans = list(plans)
+        arr = (_p * len(self.plans))(*[p.ctx for p in self.plans])
+        h = _p()
+        L = load_library()
+        st = L.vmat_batch_create(arr, len(self.plans),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                 ctypes.byref(h))
+        if st != VMAT_OK:
+            raise VmatError(st, L.vmat_last_error(None).decode())
+        self.h = h
+
+    def _chk(self, st, ok=(VMAT_OK,)):
+        if st not in ok:
+            raise VmatError(st, load_library().vmat_batch_last_error(self.h).decode())
+        return st
+
+    def configure(self, lanes):
+        self._chk(load_library().vmat_batch_configure(self.h, int(lanes)))
+
+    def tune(self, trial_iters=20, master_max_iters=100000, kkt_tol=1e-6):
+        lanes = ctypes.c_int32()
+        ms = np.zeros(4)
+        self._chk(load_library().vmat_batch_tune(self.h, int(trial_iters), int(master_max_iters),
+                                                 float(kkt_tol), ctypes.byref(lanes),
+                                                 ms.ctypes.data))
+        return lanes.value, dict(zip((1, 2, 4, 8), ms.tolist()))
+
+    def run(self, master_max_iters=100000, kkt_tol=1e-6):
+        outs, ress = [], []
+        for p in self.plans:
+            o, r = _result_arrays(p.cfg.n_angles, p.cfg.n_rows, p.cfg.n_angles)
+            outs.append(o)
+            ress.append(r)
+        res_arr = (vmat_colgen_result * len(ress))(*ress)
+        plan_ms = np.zeros(len(self.plans))
+        total = ctypes.c_double()
+        st = load_library().vmat_batch_colgen_run(self.h, int(master_max_iters), float(kkt_tol),
+                                                  res_arr, plan_ms.ctypes.data, ctypes.byref(total))
+        self._chk(st)
+        return outs, plan_ms, total.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().vmat_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
