@@ -155,18 +155,34 @@ __device__ __forceinline__ double G_inv(const double *u, const double *igr, int 
 //   D_j(t) = 2 w_j [ (c_j(t) - c_j(0)) e_j + c_j(t) t w_j ],  e_j = z_j - T_j,
 // (c = alpha below the threshold, beta above), which is O(t w_j^2) and free
 // of the cancellation that phi' itself suffers near convergence, and the
-// phi'' term 2 c_j(t) w_j^2.  FP32 per voxel, FP32 within a warp, FP64 across
-// warps and CTAs in a fixed order.  Out: s_res[0..15] = sum_j D_j(t_p),
-// s_res[16..31] = sum_j 2 c_j(t_p) w_j^2.
+// phi'' term 2 c_j(t) w_j^2.  Along the direction a voxel changes side at
+// most once, at t_j = -e_j / w_j, and only if e_j and w_j have opposite
+// signs; before it D_j(t) = 2 c_j(0) w_j^2 t, after it the term
+// k_j (e_j + t w_j), k_j = 2 w_j (c_side - c_j(0)), is added.  So a voxel
+// whose change lies before every trial point (or nowhere) adds a linear
+// function of t, kept in three per-thread sums, and only voxels that change
+// side between the first and last trial point are evaluated point by point.
+// FP32 per voxel, FP32 within a warp, FP64 across warps and CTAs in a fixed
+// order.  Out: s_res[0..15] = sum_j D_j(t_p), s_res[16..31] = sum_j
+// 2 c_j(t_p) w_j^2.
 template <int VPT>
 __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[VPT],
                                          const float (&w)[VPT], const uint8_t (&sid)[VPT],
                                          const float *s_tab, const float *s_t, float *s_ls,
                                          double *s_res, int *s_ok, int parity, int stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  float t_first = s_t[0], t_last = s_t[0];
+#pragma unroll
+  for (int p = 1; p < LS_POINTS; ++p) {
+    t_first = fminf(t_first, s_t[p]);
+    t_last = fmaxf(t_last, s_t[p]);
+  }
   float v[32];
 #pragma unroll
   for (int p = 0; p < 32; ++p) v[p] = 0.f;
+  float lin = 0.f;    // sum 2 c_j(0) w_j^2 over the thread's voxels
+  float jump = 0.f;   // sum 2 w_j^2 (c_side - c_j(0)) over changes before t_first
+  float at_first = 0.f;  // sum k_j (e_j + t_first w_j) over the same voxels
 #pragma unroll
   for (int q = 0; q < VPT; ++q) {
     const float wq = w[q];
@@ -176,15 +192,31 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     const float e0 = z[q] - T;
     const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
     const float c0 = e0 > 0.f ? be : (e0 < 0.f ? al : cw);
+    lin = fmaf(2.f * c0 * wq, wq, lin);
+    const float dc = cw - c0;  // nonzero only if the voxel can change side
+    if (dc == 0.f) continue;
+    const float k = 2.f * wq * dc, dh = k * wq;
+    const float e_first = fmaf(t_first, wq, e0);
+    if (e_first * wq > 0.f) {  // changed side before every trial point
+      jump += dh;
+      at_first = fmaf(k, e_first, at_first);
+      continue;
+    }
+    if (!(fmaf(t_last, wq, e0) * wq > 0.f)) continue;  // after every trial point
 #pragma unroll
     for (int p = 0; p < LS_POINTS; ++p) {
-      const float tp = s_t[p];
-      const float e = fmaf(tp, wq, e0);
-      const float c = e > 0.f ? be : (e < 0.f ? al : cw);
-      const float twq = 2.f * wq;
-      v[p] = fmaf(twq, fmaf(c - c0, e0, c * tp * wq), v[p]);
-      v[LS_POINTS + p] = fmaf(twq * c, wq, v[LS_POINTS + p]);
+      const float e = fmaf(s_t[p], wq, e0);
+      if (e * wq > 0.f) {
+        v[p] = fmaf(k, e, v[p]);
+        v[LS_POINTS + p] += dh;
+      }
     }
+  }
+#pragma unroll
+  for (int p = 0; p < LS_POINTS; ++p) {
+    const float tp = s_t[p];
+    v[p] += fmaf(lin, tp, fmaf(jump, tp - t_first, at_first));
+    v[LS_POINTS + p] += lin + jump;
   }
   const float ws = warp_transpose_sum32(v);
   s_ls[warp * 32 + lane] = ws;

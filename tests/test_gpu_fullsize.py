@@ -1,0 +1,214 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (FP32 D uploaded from FP32 values, default master launch).
+
+Prostate phantom (128x128x64 voxels, 180 beams, 40x40 MLC, 4.5e8 nonzeros):
+dose, price, pricing, aperture columns and the first column-generation
+iterations element by element against the FP64 oracle; the whole
+180-iteration plan through properties that hold at any size (every beam once,
+leaf travel within the limits, cost never rising, its dose and cost equal to
+the oracle's for the same apertures and intensities, and the KKT residual of
+its last master problem within FP32 reach of zero).
+
+Head-and-neck phantom (160x160x96 voxels, 180 beams, 60x40 MLC, 6.3e8
+nonzeros): FP32, FP16 and BF16 storage of D against the FP64 dose of a
+deliverable plan scaled to the prescription (Sec. 2.1, Eq. 1)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_4396_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1005_4396_b300 import vmat  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def prostate():
+    return inputs.make_problem(inputs.prostate_config())
+
+
+@pytest.fixture(scope="module")
+def pplan(prostate):
+    p = vmat.Plan(prostate, val_f32=True)
+    yield p
+    p.close()
+
+
+def _cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _random_deliverable(cfg, rng, beams):
+    """Apertures for `beams`, placed one at a time, each row drawn inside the
+    leaf-travel limits of the beams already placed (Sec. 2.2)."""
+    N, R, C, s = cfg.n_angles, cfg.n_rows, cfg.n_cols, cfg.max_leaf_step
+    occ = np.zeros(N, np.uint8)
+    ll = np.zeros(N * R, np.int16)
+    rr = np.zeros(N * R, np.int16)
+    for k in beams:
+        Llo, Lhi, Rlo, Rhi = oracle.leaf_limits(N, R, C, s, cfg.cyclic, occ, ll, rr, k)
+        for row in range(R):
+            top = min(Lhi[row], Rhi[row])
+            assert Llo[row] <= top
+            l = int(rng.integers(Llo[row], top + 1))
+            r = int(rng.integers(max(l, Rlo[row]), Rhi[row] + 1))
+            ll[k * R + row], rr[k * R + row] = l, r
+        occ[k] = 1
+    return occ, ll, rr
+
+
+def _leaves(a, k, R):
+    return a[k * R:(k + 1) * R]
+
+
+# ------------------------------------------------------------------ prostate
+def test_prostate_sizes(prostate, pplan):
+    inf = pplan.info
+    assert inf["n_vox"] == prostate.n_vox == 128 * 128 * 64
+    assert inf["n_beamlets"] == 288000 and inf["nnz"] == prostate.nnz
+    assert inf["n_active"] == np.unique(prostate.vox_idx).size
+
+
+def test_prostate_dose_and_price(prostate, pplan):
+    x = inputs.rng.uniform(101, prostate.n_beamlets).astype(np.float32)
+    z, fp, cost = pplan.dose(_cuda(x))
+    z_or = oracle.dose(prostate, x.astype(np.float64))
+    zmax = np.abs(z_or).max()
+    np.testing.assert_allclose(z.cpu().numpy(), z_or, rtol=1e-5, atol=1e-6 * zmax)
+    c_or = oracle.voxel_cost(z_or, prostate.struct_id, prostate.T, prostate.alpha, prostate.beta)
+    assert cost == pytest.approx(c_or, rel=1e-5)
+    # price of a signed voxel vector at half of the beams
+    f = inputs.rng.normal(102, prostate.n_vox).astype(np.float32)
+    mask = (np.arange(prostate.cfg.n_angles) % 2 == 0).astype(np.uint8)
+    g = pplan.price(_cuda(f), mask).cpu().numpy()
+    f64 = f.astype(np.float64)
+    g_or = oracle.price(prostate, f64, mask)
+    scale = oracle.price(prostate, np.abs(f64), mask)
+    assert np.all(np.abs(g - g_or) <= 1e-5 * scale + 1e-30)
+    beam = np.arange(prostate.n_beamlets) // (prostate.cfg.n_rows * prostate.cfg.n_cols)
+    assert np.all(g[mask[beam] == 0] == 0)
+
+
+def test_prostate_pricing_bit_exact_and_columns(prostate, pplan):
+    cfg = prostate.cfg
+    R = cfg.n_rows
+    rng = np.random.default_rng(103)
+    beams = [int(k) for k in rng.permutation(cfg.n_angles)[:90]]
+    occ, ll, rr = _random_deliverable(cfg, rng, beams)
+    pplan.reset()
+    for k in beams:
+        pplan.add_column(k, _leaves(ll, k, R), _leaves(rr, k, R))
+    for trial in range(3):
+        g = rng.normal(size=prostate.n_beamlets).astype(np.float32)
+        if trial == 1:  # exact zero prices: exact ties
+            g[rng.uniform(size=g.size) < 0.5] = 0.0
+        got = pplan.pricing_select(_cuda(g))
+        ref = oracle.pricing(cfg, occ, ll, rr, g.astype(np.float64), f32=True)
+        assert got["k"] == ref["k"]
+        np.testing.assert_array_equal(got["l"], ref["l"])
+        np.testing.assert_array_equal(got["r"], ref["r"])
+        assert got["p"] == ref["p"] and got["p2"] == ref["p2"]
+    # aperture-dose columns of three of the placed beams
+    for k in beams[:3]:
+        y = np.zeros(cfg.n_angles)
+        y[k] = 1.0
+        pplan.master_step(max_iters=0, kkt_tol=0.0, y=y)
+        z = pplan.plan_dose().cpu().numpy()
+        col = oracle.aperture_dose(prostate, k, _leaves(ll, k, R), _leaves(rr, k, R))
+        np.testing.assert_allclose(z, col, rtol=1e-5, atol=1e-6 * col.max())
+    pplan.reset()
+
+
+def _first_difference(gpu, ref, R, tol=1e-6):
+    for t in range(len(ref["k"])):
+        k = ref["k"][t]
+        same = gpu["k"][t] == k and np.array_equal(_leaves(gpu["lleaf"], k, R), _leaves(ref["lleaf"], k, R)) \
+            and np.array_equal(_leaves(gpu["rleaf"], k, R), _leaves(ref["rleaf"], k, R))
+        if not same:
+            assert min(ref["margin"][t], ref["row_margin"][t]) <= tol, f"iteration {t} differs off a tie"
+            return t
+    return len(ref["k"])
+
+
+def test_prostate_first_iterations(prostate, pplan):
+    cfg = prostate.cfg
+    R, n = cfg.n_rows, 6
+    ref = oracle.colgen(prostate, n_iter=n, eps=1e-8)
+    pplan.reset()
+    gpu = pplan.colgen_run(n_iters=n, kkt_tol=1e-6)
+    first = _first_difference(gpu, ref, R)
+    np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
+    # the oracle's decisions replayed on the GPU: every master cost within 1e-5
+    fl = np.array([_leaves(ref["lleaf"], k, R) for k in ref["k"]])
+    fr = np.array([_leaves(ref["rleaf"], k, R) for k in ref["k"]])
+    pplan.reset()
+    rep = pplan.colgen_run(n_iters=n, kkt_tol=1e-6, forced=(ref["k"], fl, fr))
+    np.testing.assert_array_equal(rep["k"], ref["k"])
+    np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
+    pplan.reset()
+
+
+def test_prostate_whole_plan(prostate, pplan):
+    cfg = prostate.cfg
+    N, R, C, s = cfg.n_angles, cfg.n_rows, cfg.n_cols, cfg.max_leaf_step
+    pplan.reset()
+    out = pplan.colgen_run(kkt_tol=max(cfg.kkt_eps, 1e-6))
+    assert sorted(out["k"].tolist()) == list(range(N))
+    y, ll, rr = out["y"], out["lleaf"], out["rleaf"]
+    assert np.all(y >= 0)
+    assert np.all(np.diff(out["cost"]) <= 1e-6 * out["cost"][0])
+    full = np.ones(N, np.uint8)
+    for k in range(N):  # each aperture inside the travel limits of its final neighbours
+        occ = full.copy()
+        occ[k] = 0
+        Llo, Lhi, Rlo, Rhi = oracle.leaf_limits(N, R, C, s, cfg.cyclic, occ, ll, rr, k)
+        l, r = _leaves(ll, k, R), _leaves(rr, k, R)
+        assert np.all((Llo <= l) & (l <= Lhi) & (Rlo <= r) & (r <= Rhi) & (l <= r)), k
+    # the plan's dose and cost are those of its own apertures and intensities
+    z = pplan.plan_dose().cpu().numpy()
+    z_or = oracle.dose(prostate, oracle.aperture_fluence(cfg, ll, rr, y))
+    np.testing.assert_allclose(z, z_or, rtol=1e-5, atol=1e-6 * z_or.max())
+    sid, T, al, be = prostate.struct_id, prostate.T, prostate.alpha, prostate.beta
+    c_or = oracle.voxel_cost(z_or, sid, T, al, be) + cfg.gamma * oracle.G(prostate.theta_deg, y, cfg.cyclic)
+    assert out["cost"][-1] == pytest.approx(c_or, rel=1e-5)
+    # KKT of the last master problem (Sec. 2.2): rho = max_k |min(y_k, g_k)| is
+    # within FP32 reach of zero, with g from the oracle's own columns
+    M = np.array([oracle.aperture_dose(prostate, k, _leaves(ll, k, R), _leaves(rr, k, R))
+                  for k in range(N)])
+    fp = oracle.voxel_dcost(z_or, sid, T, al, be)
+    g = M @ fp + cfg.gamma * oracle.dG(prostate.theta_deg, y, cfg.cyclic)
+    rho = np.abs(np.minimum(y, g)).max()
+    reach = (M @ np.abs(fp)).max()  # sum_j |M_kj F'_j|: the scale of FP32 rounding in g
+    fp0 = oracle.voxel_dcost(np.zeros(prostate.n_vox), sid, T, al, be)
+    rho_plan = (M @ np.abs(fp0)).max()  # bounds the first master's starting residual
+    assert rho <= 1e-5 * reach + 2e-6 * rho_plan, (rho, reach, rho_plan)
+    pplan.reset()
+
+
+# ------------------------------------------------------------------ head and neck
+def test_headneck_reduced_precision_dose():
+    cfg = inputs.headneck_config()
+    prob = inputs.make_problem(cfg)
+    N, R = cfg.n_angles, cfg.n_rows
+    rng = np.random.default_rng(104)
+    occ, ll, rr = _random_deliverable(cfg, rng, [int(k) for k in rng.permutation(N)])
+    y = rng.uniform(0.5, 1.5, N)
+    z = oracle.dose(prob, oracle.aperture_fluence(cfg, ll, rr, y))
+    rx = prob.T.max()
+    tgt = prob.T[prob.struct_id] == rx
+    y *= rx / z[tgt].mean()  # mean dose of the first target at its prescription
+    x = oracle.aperture_fluence(cfg, ll, rr, y)
+    z64 = oracle.dose(prob, x)
+    errs = {}
+    for dt in ("f32", "f16", "bf16"):
+        with vmat.Plan(prob, dtype=dt, val_f32=True) as plan:
+            zg = plan.dose(_cuda(x.astype(np.float32)))[0].cpu().numpy()
+        errs[dt] = np.abs(zg - z64).max() / rx
+        if dt == "f32":
+            np.testing.assert_allclose(zg, z64, rtol=1e-5, atol=1e-6 * z64.max())
+    assert errs["f16"] <= 5e-3 and errs["bf16"] <= 5e-3, errs
