@@ -114,21 +114,14 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Warp transpose-reduction: v[32] per lane in, lane l returns the warp sum of
-// v[l] (31 shuffles for 32 sums).
-__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 16; k >= 1; k >>= 1) {
-    const bool upper = (lane & k) != 0;
-#pragma unroll
-    for (int i = 0; i < k; ++i) {
-      const float send = upper ? v[i] : v[i + k];
-      const float keep = upper ? v[i + k] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
-    }
-  }
-  return v[0];
+// Compensated FP32 accumulation (Neumaier's variant of Kahan summation): s
+// holds the running sum, c the rounding error it has dropped; s + c carries
+// about twice the precision of s, so a few hundred terms sum to FP64-like
+// accuracy on the FP32 pipe (FP64 issues at a small fraction of its rate).
+__device__ __forceinline__ void comp_add(float &s, float &c, float x) {
+  const float t = __fadd_rn(s, x);
+  c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s));
+  s = t;
 }
 
 // derivative of the smoothing term G (Eq. 2) at beam k, from inverse gaps
@@ -162,14 +155,24 @@ __device__ __forceinline__ double G_inv(const double *u, const double *igr, int 
 // whose change lies before every trial point (or nowhere) adds a linear
 // function of t, kept in three per-thread sums, and only voxels that change
 // side between the first and last trial point are evaluated point by point.
-// FP32 per voxel, FP32 within a warp, FP64 across warps and CTAs in a fixed
-// order.  Out: s_res[0..15] = sum_j D_j(t_p), s_res[16..31] = sum_j
-// 2 c_j(t_p) w_j^2.
+// FP32 per voxel and within a warp, compensated FP32 across warps and CTAs
+// in a fixed order.  Out, in lane l of warp 0 (lsv): sum_j D_j(t_l) for
+// l < 16, sum_j 2 c_j(t_{l-16}) w_j^2 for l >= 16.
+// The point-by-point sums live in a padded shared-memory row per thread
+// (s_row, 33 floats), not in registers: they are touched only by the few
+// voxels inside the bracket, and the registers stay free for z and w.
+// structure id of the thread's voxel v (4 ids packed per word)
+template <int NW>
+__device__ __forceinline__ int sid_of(const uint32_t (&sidw)[NW], int v) {
+  return (int)((sidw[v >> 2] >> (8 * (v & 3))) & 0xffu);
+}
+
 template <int VPT>
 __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[VPT],
-                                         const float (&w)[VPT], const uint8_t (&sid)[VPT],
-                                         const float *s_tab, const float *s_t, float *s_ls,
-                                         double *s_res, int *s_ok, int parity, int stride) {
+                                         const float (&w)[VPT], const uint32_t (&sid)[VPT / 4],
+                                         const float *s_tab, const float *s_t, float *s_rows,
+                                         float *s_ls, double *s_res, int *s_ok, int parity,
+                                         int stride, double &lsv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   float t_first = s_t[0], t_last = s_t[0];
 #pragma unroll
@@ -177,9 +180,8 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     t_first = fminf(t_first, s_t[p]);
     t_last = fmaxf(t_last, s_t[p]);
   }
-  float v[32];
-#pragma unroll
-  for (int p = 0; p < 32; ++p) v[p] = 0.f;
+  float *v = s_rows + threadIdx.x * 33;  // all zero on entry; left zero on exit
+  bool touched = false;
   float lin = 0.f;    // sum 2 c_j(0) w_j^2 over the thread's voxels
   float jump = 0.f;   // sum 2 w_j^2 (c_side - c_j(0)) over changes before t_first
   float at_first = 0.f;  // sum k_j (e_j + t_first w_j) over the same voxels
@@ -187,7 +189,7 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
   for (int q = 0; q < VPT; ++q) {
     const float wq = w[q];
     if (wq == 0.f) continue;
-    const int id = sid[q];
+    const int id = sid_of(sid, q);
     const float T = s_tab[id], al = s_tab[256 + id], be = s_tab[512 + id];
     const float e0 = z[q] - T;
     const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
@@ -203,6 +205,7 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
       continue;
     }
     if (!(fmaf(t_last, wq, e0) * wq > 0.f)) continue;  // after every trial point
+    touched = true;
 #pragma unroll
     for (int p = 0; p < LS_POINTS; ++p) {
       const float e = fmaf(s_t[p], wq, e0);
@@ -212,35 +215,59 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
       }
     }
   }
+  // lane l sums entry l of the warp's touched rows, in lane order
+  // (conflict-free: row stride 33), and each touched row is zeroed again
+  const unsigned rows = __ballot_sync(0xffffffffu, touched);
+  float ws = 0.f;
+  if (rows) {
+    __syncwarp();
+    const float *col = s_rows + warp * 32 * 33 + lane;
+    for (unsigned m = rows; m; m &= m - 1) ws += col[(__ffs(m) - 1) * 33];
+    __syncwarp();
+    if (touched)
 #pragma unroll
-  for (int p = 0; p < LS_POINTS; ++p) {
-    const float tp = s_t[p];
-    v[p] += fmaf(lin, tp, fmaf(jump, tp - t_first, at_first));
-    v[LS_POINTS + p] += lin + jump;
+      for (int p = 0; p < 32; ++p) v[p] = 0.f;
   }
-  const float ws = warp_transpose_sum32(v);
+  lin = warp_sumf(lin);
+  jump = warp_sumf(jump);
+  at_first = warp_sumf(at_first);
+  const float tp = s_t[lane & (LS_POINTS - 1)];
+  ws += lane < LS_POINTS ? fmaf(lin, tp, fmaf(jump, tp - t_first, at_first)) : lin + jump;
   s_ls[warp * 32 + lane] = ws;
   __syncthreads();
   const int off = LS_OFF(a.N, parity);
-  if (warp == 0) {
-    double acc = 0.0;
-    for (int q = 0; q < nwarp; ++q) acc += (double)s_ls[q * 32 + lane];
-    a.part[(size_t)blockIdx.x * stride + off + lane] = acc;
+  if (warp == 0) {  // the CTA's 32 sums, compensated over its warps, as FP32
+    float cs = 0.f, cc = 0.f;
+    for (int q = 0; q < nwarp; ++q) comp_add(cs, cc, s_ls[q * 32 + lane]);
+    ((float *)(a.part + (size_t)blockIdx.x * stride + off))[lane] = __fadd_rn(cs, cc);
   }
   if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_ok)) return false;
-  // sum the CTAs' partials: thread (warp, lane) takes CTAs warp, warp + W, ...
-  double acc = 0.0;
-  for (int c = warp; c < (int)gridDim.x; c += nwarp)
-    acc += __ldcg(a.part + (size_t)c * stride + off + lane);
-  double *s_tmp = s_res + 32;  // [nwarp][32]
-  s_tmp[warp * 32 + lane] = acc;
+  // sum the CTAs' partials: warp w takes CTAs w, w + W, ... (8 loads in flight
+  // per lane), compensated; then warp 0 combines the warps in order
+  const int G = gridDim.x;
+  float cs = 0.f, cc = 0.f;
+  for (int c0 = warp; c0 < G; c0 += 8 * nwarp) {
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * nwarp;
+      x[u] = c < G ? __ldcg((const float *)(a.part + (size_t)c * stride + off) + lane) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) comp_add(cs, cc, x[u]);
+  }
+  float2 *s_w2 = (float2 *)(s_res + 32);  // [nwarp][32]
+  s_w2[warp * 32 + lane] = make_float2(cs, cc);
   __syncthreads();
   if (warp == 0) {
-    double r = 0.0;
-    for (int q = 0; q < nwarp; ++q) r += s_tmp[q * 32 + lane];
-    s_res[lane] = r;
+    float S = 0.f, C = 0.f;
+    for (int q = 0; q < nwarp; ++q) {
+      const float2 v = s_w2[q * 32 + lane];
+      comp_add(S, C, v.x);
+      C = __fadd_rn(C, v.y);
+    }
+    lsv = (double)S + (double)C;
   }
-  __syncthreads();
   return true;
 }
 
@@ -263,16 +290,17 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   double *s_dy = s_gold + N;         // [N] per slot
   double *s_igl = s_dy + N;          // [N] 1/gap to the left neighbour (0: none)
   double *s_igr = s_igl + N;         // [N] 1/gap to the right neighbour (0: none)
-  double *s_dgy = s_igr + N;         // [N] per slot: dG(y) at the slot's beam
-  double *s_sc = s_dgy + N;          // [32] CTA-wide scalars
+  int *s_slot = (int *)(s_igr + N);  // [N] slot of each beam, -1 if none (N doubles reserved)
+  double *s_sc = s_igr + 2 * N;      // [32] CTA-wide scalars
   double *s_res = s_sc + 32;         // [32 + 16*32] line-search sums and scratch
   float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [N] per slot
   float *s_df = s_yf + N;                         // [N] per slot
   float *s_tab = s_df + N;                        // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
   float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
-  float *s_fp = s_ls + 16 * 32;                   // [NG][ST] F' of the CTA's subtiles
-  float *s_pp = s_fp + NG * ST;                   // [N*NG] warp partial per (slot, subtile) pair
+  float *s_fp = s_ls + 16 * 32;                   // [NG][ST] F' of the CTA's subtiles (pass A)
+  float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
+  float *s_pp = s_rows + 33 * nthr;               // [N*NG] warp partial per (slot, subtile) pair
   int *s_i = (int *)(s_pp + N * NG);              // [8]: 1 nonzero slots, 2 nonzero pairs
   int *s_beam = s_i + 8;                          // [N] beam of slot
   int *s_nz = s_beam + N;                         // [N] slots with a nonzero subtile here
@@ -281,6 +309,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   int *s_pair = s_pst + N + 1;                    // [N*NG] pairs s*8+m in slot order
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
+  for (int q = tid; q < 33 * nthr; q += nthr) s_rows[q] = 0.f;
   for (int k = tid; k < N; k += nthr) {
     s_y[k] = a.y[k];
     s_d[k] = 0.0;
@@ -290,8 +319,11 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     s_igr[k] = hr ? 1.0 / (k < N - 1 ? a.theta[k + 1] - a.theta[k] : a.theta[0] + 360.0 - a.theta[N - 1])
                   : 0.0;
   }
+  for (int k = tid; k < N; k += nthr) s_slot[k] = -1;
+  __syncthreads();
   for (int s = tid; s < ns; s += nthr) {
     s_beam[s] = a.slot_beam[s];
+    s_slot[a.slot_beam[s]] = s;
     s_dy[s] = 0.0;
     s_gold[s] = 0.0;
   }
@@ -319,18 +351,16 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   for (int s = tid; s < ns; s += nthr) s_yf[s] = (float)s_y[s_beam[s]];
   const int nnzs = s_i[1], npairs = s_i[2];
 
-  uint8_t my_sid[VPT];
+  uint32_t my_sid[NG];
 #pragma unroll
-  for (int m = 0; m < NG; ++m)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) my_sid[4 * m + q] = a.sid[SUB_OFF(m) + 4 * tid + q];
+  for (int m = 0; m < NG; ++m) my_sid[m] = __ldg((const uint32_t *)(a.sid + SUB_OFF(m)) + tid);
   float z[VPT], w[VPT];
   __syncthreads();
 
   // z = M y
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
-#pragma unroll 4
+#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
   for (int q = 0; q < nnzs; ++q) {
     const int s = s_nz[q], mk = s_mask[s];
     const float *Ms = a.M + (size_t)s * a.Vpad;
@@ -350,22 +380,25 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   double rho = 0.0, rho0 = 0.0, tol = 0.0;
   bool alive = true;
   int ls_parity = 0;
-  unsigned long long tA = 0, tS = 0, tB = 0, tL = 0, c0 = 0;
+  // phase clocks of CTA 0, kept in shared memory (one thread uses them)
+  unsigned long long *s_clk = (unsigned long long *)(s_sc + 24);  // [5]: A, step, B, search, last
   const bool timer = blockIdx.x == 0 && tid == 0;
+  if (timer)
+    for (int q = 0; q < 5; ++q) s_clk[q] = 0;
 
   for (;;) {
-    if (timer) c0 = vmat_globaltimer();
+    if (timer) s_clk[4] = vmat_globaltimer();
     // ---------------- pass A: per-slot CTA partials of M^T F'(z)
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
       float4 f;
-      int id = my_sid[4 * m];
+      int id = sid_of(my_sid, 4 * m);
       f.x = vmat_dF(z[4 * m], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
-      id = my_sid[4 * m + 1];
+      id = sid_of(my_sid, 4 * m + 1);
       f.y = vmat_dF(z[4 * m + 1], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
-      id = my_sid[4 * m + 2];
+      id = sid_of(my_sid, 4 * m + 2);
       f.z = vmat_dF(z[4 * m + 2], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
-      id = my_sid[4 * m + 3];
+      id = sid_of(my_sid, 4 * m + 3);
       f.w = vmat_dF(z[4 * m + 3], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
       *(float4 *)(s_fp + m * ST + 4 * tid) = f;
     }
@@ -404,79 +437,113 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     }
     ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
-    if (timer) { unsigned long long c1 = vmat_globaltimer(); tA += c1 - c0; c0 = c1; }
+    if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[0] += c1 - s_clk[4]; s_clk[4] = c1; }
 
     // ---------------- gradient, residual, direction (same in every CTA)
-    for (int s = tid; s < ns; s += nthr) {
-      const double dg = dG_inv(s_y, s_igl, s_igr, N, s_beam[s]);
-      s_dgy[s] = dg;
-      s_g[s] = __ldcg(a.gred + s) + a.gamma * dg;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double r = 0.0, ym = 0.0, gm = 0.0, dyg = 0.0, dgg = 0.0;
-      for (int s = lane; s < ns; s += 32) {
-        const double yk = s_y[s_beam[s]], gk = s_g[s];
-        r = fmax(r, fabs(fmin(yk, gk)));
-        ym = fmax(ym, fabs(yk));
-        gm = fmax(gm, fabs(gk));
-        const double dg = gk - s_gold[s];
-        dyg += s_dy[s] * dg;
-        dgg += dg * dg;
+    // y, g and d are formed in FP64, spread over all threads.  The KKT
+    // residual and the magnitudes are maxima, taken exactly on the bit
+    // patterns of the FP64 values (integer compares; y >= 0 always); the
+    // Barzilai-Borwein inner products, phi'(0) = g.d (all terms <= 0) and G(d)
+    // are taken in FP32.  Reductions: warp butterflies, then every thread
+    // combines the warps' values in the same order.
+    {
+      const unsigned FULL = 0xffffffffu;
+      const unsigned long long ABS = 0x7fffffffffffffffull;
+      unsigned long long rb = 0, yb = 0, gb = 0;
+      float dyg = 0.f, dgg = 0.f;
+      for (int s = tid; s < ns; s += nthr) {
+        const int k = s_beam[s];
+        const double gk = __ldcg(a.gred + s) + a.gamma * dG_inv(s_y, s_igl, s_igr, N, k);
+        s_g[s] = gk;
+        const unsigned long long ybits = (unsigned long long)__double_as_longlong(s_y[k]) & ABS;
+        const unsigned long long gbits = (unsigned long long)__double_as_longlong(gk);
+        const unsigned long long gabs = gbits & ABS;
+        rb = max(rb, (gbits >> 63) ? gabs : min(ybits, gabs));  // |min(y, g)|
+        yb = max(yb, ybits);
+        gb = max(gb, gabs);
+        const float dgk = (float)(gk - s_gold[s]), dyk = (float)s_dy[s];
+        dyg = fmaf(dyk, dgk, dyg);
+        dgg = fmaf(dgk, dgk, dgg);
       }
-      r = warp_max(r);
-      ym = warp_max(ym);
-      gm = warp_max(gm);
-      dyg = warp_sum(dyg);
-      dgg = warp_sum(dgg);
+      for (int o = 16; o; o >>= 1) {
+        rb = max(rb, __shfl_xor_sync(FULL, rb, o));
+        yb = max(yb, __shfl_xor_sync(FULL, yb, o));
+        gb = max(gb, __shfl_xor_sync(FULL, gb, o));
+        dyg += __shfl_xor_sync(FULL, dyg, o);
+        dgg += __shfl_xor_sync(FULL, dgg, o);
+      }
+      unsigned long long *s_ru = (unsigned long long *)(s_res + 32);  // [3][16]
+      float *s_rf = (float *)(s_res + 32 + 48);                       // [2][16]
       if (lane == 0) {
-        s_sc[0] = r;
-        double step;
-        if (it == 0) step = fmax(ym, 1.0) / fmax(gm, 1e-300);
-        else step = (dyg > 0.0 && dgg > 0.0) ? dyg / dgg : 1e12;
-        s_sc[1] = fmin(fmax(step, 1e-12), 1e12);
+        s_ru[warp] = rb;
+        s_ru[16 + warp] = yb;
+        s_ru[32 + warp] = gb;
+        s_rf[warp] = dyg;
+        s_rf[16 + warp] = dgg;
+      }
+      __syncthreads();
+      rb = yb = gb = 0;
+      dyg = dgg = 0.f;
+      for (int q = 0; q < nwarp; ++q) {
+        rb = max(rb, s_ru[q]);
+        yb = max(yb, s_ru[16 + q]);
+        gb = max(gb, s_ru[32 + q]);
+        dyg += s_rf[q];
+        dgg += s_rf[16 + q];
+      }
+      rho = __longlong_as_double((long long)rb);
+      if (it == 0) {
+        rho0 = rho;
+        const double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
+        tol = a.kkt_tol * fmax(fmax(rho0, ref), 1e-300);
+      }
+      if (rho <= tol) { status = VMAT_OK; break; }
+      if (it >= a.max_iters) { status = VMAT_ENOTCONV; break; }
+      double step;
+      if (it == 0)
+        step = fmax(__longlong_as_double((long long)yb), 1.0) /
+               fmax(__longlong_as_double((long long)gb), 1e-300);
+      else
+        step = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
+      step = fmin(fmax(step, 1e-12), 1e12);
+      float g0 = 0.f;
+      for (int s = tid; s < ns; s += nthr) {
+        const int k = s_beam[s];
+        const double yk = s_y[k], gk = s_g[s];
+        const double p = yk - step * gk;
+        const double dk = (p > 0.0 ? p : 0.0) - yk;
+        s_d[k] = dk;
+        s_df[s] = (float)dk;
+        s_gold[s] = gk;
+        g0 = fmaf((float)gk, (float)dk, g0);
+      }
+      if (tid == 0) {  // line-search bracket [0, 1]; phi'(0) is filled in by warp 0
+        double *st = s_sc + 8;
+        st[0] = 0.0; st[1] = 0.0; st[2] = -1.0; st[3] = 1.0;
+        st[4] = 0.0; st[5] = -1.0; st[6] = -1.0; st[7] = 0.0;
+      }
+      __syncthreads();
+      float gdd = 0.f;  // G(d) over the beam pairs (unoccupied beams have d = 0)
+      for (int k = tid; k < N; k += nthr) {
+        const int kp = k < N - 1 ? k + 1 : 0;  // s_igr[N-1] = 0 on a path
+        const float dd = (float)(s_d[kp] - s_d[k]);
+        gdd = fmaf(dd * dd, (float)s_igr[k], gdd);
+      }
+      for (int o = 16; o; o >>= 1) {
+        g0 += __shfl_xor_sync(FULL, g0, o);
+        gdd += __shfl_xor_sync(FULL, gdd, o);
+      }
+      if (lane == 0) {  // summed over warps by warp 0 in the line search
+        ((float *)s_sc)[warp] = g0;               // s_sc[0..7]
+        ((float *)(s_sc + 16))[warp] = gdd;       // s_sc[16..23]
       }
     }
-    __syncthreads();
-    rho = s_sc[0];
-    if (it == 0) {
-      rho0 = rho;
-      const double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
-      tol = a.kkt_tol * fmax(fmax(rho0, ref), 1e-300);
-    }
-    if (rho <= tol) { status = VMAT_OK; break; }
-    if (it >= a.max_iters) { status = VMAT_ENOTCONV; break; }
-    const double step = s_sc[1];
-    for (int s = tid; s < ns; s += nthr) {
-      const int k = s_beam[s];
-      const double yk = s_y[k];
-      const double p = yk - step * s_g[s];
-      const double dk = (p > 0.0 ? p : 0.0) - yk;
-      s_d[k] = dk;
-      s_df[s] = (float)dk;
-      s_gold[s] = s_g[s];
-    }
-    __syncthreads();
-    if (warp == 0) {  // g.d (full gradient: phi'(0)), dG(y).d and G(d)
-      double gd = 0.0, g0 = 0.0;
-      for (int s = lane; s < ns; s += 32) {
-        const double dk = s_d[s_beam[s]];
-        gd += s_dgy[s] * dk;
-        g0 += s_g[s] * dk;
-      }
-      gd = warp_sum(gd);
-      g0 = warp_sum(g0);
-      const double Gd = G_inv(s_d, s_igr, N);
-      if (lane == 0) { s_sc[2] = gd; s_sc[3] = Gd; s_sc[4] = g0; }
-    }
-    __syncthreads();
-    const double gdot = s_sc[2], Gd = s_sc[3], phi0 = s_sc[4];
-    if (timer) { unsigned long long c1 = vmat_globaltimer(); tS += c1 - c0; c0 = c1; }
+    if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[1] += c1 - s_clk[4]; s_clk[4] = c1; }
 
     // ---------------- pass B: z = M y, w = M d
 #pragma unroll
     for (int v = 0; v < VPT; ++v) { z[v] = 0.f; w[v] = 0.f; }
-#pragma unroll 4
+#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
     for (int q = 0; q < nnzs; ++q) {
       const int s = s_nz[q], mk = s_mask[s];
       const float *Ms = a.M + (size_t)s * a.Vpad;
@@ -491,79 +558,118 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]); w[4 * m + 3] = fmaf(q.w, ds, w[4 * m + 3]);
       }
     }
-    if (timer) { unsigned long long c1 = vmat_globaltimer(); tB += c1 - c0; c0 = c1; }
+    if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[2] += c1 - s_clk[4]; s_clk[4] = c1; }
 
     // ---------------- exact line search on [0, 1]
     // phi'(t) = phi'(0) + sum_j D_j(t) + 2 gamma G(d) t, phi'(0) = g.d from the
-    // reduced gradient; thread 0 keeps the bracket [lo, hi] (phi'(lo) < 0 <
-    // phi'(hi)) and picks the trial points; all CTAs see the same sums.
-    const double cg1 = 2.0 * a.gamma * Gd;
+    // reduced gradient; warp 0 keeps the bracket [lo, hi] (phi'(lo) < 0 <
+    // phi'(hi)) and threads 0..15 pick the trial points; all CTAs see the
+    // same sums and take the same decisions.
     double *s_ls_state = s_sc + 8;  // lo_t lo_f lo_h hi_t hi_f hi_h t done
-    if (tid == 0) {
-      s_ls_state[0] = 0.0; s_ls_state[1] = phi0; s_ls_state[2] = -1.0;
-      s_ls_state[3] = 1.0; s_ls_state[4] = 0.0; s_ls_state[5] = -1.0;
-      s_ls_state[6] = -1.0; s_ls_state[7] = phi0 < 0.0 ? 0.0 : 1.0;
-      if (!(phi0 < 0.0)) s_ls_state[6] = 0.0;  // not a descent direction
-    }
-    __syncthreads();
+    double phi0 = 0.0, cg1 = 0.0;   // phi'(0) and 2 gamma G(d): warp 0, from round 0 on
     for (int r = 0; r < LS_ROUNDS && s_ls_state[7] == 0.0; ++r) {
-      if (tid < LS_POINTS) {
-        const double lo_t = s_ls_state[0], lo_f = s_ls_state[1], lo_h = s_ls_state[2];
-        const double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
-        double tq;
+      if (tid < LS_POINTS) {  // trial points (FP32, as they are stored)
+        float tq;
         if (r == 0) {
-          tq = (double)(tid + 1) / (double)LS_POINTS;  // 1/16 .. 1
+          tq = (float)(tid + 1) * (1.f / LS_POINTS);  // 1/16 .. 1
         } else {
-          const double span = hi_t - lo_t;
-          if (tid == 0) tq = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
-          else if (tid == 1) tq = hi_h > 0.0 ? hi_t - hi_f / hi_h : -1.0;
-          else tq = lo_t + span * (double)(tid - 1) / (double)(LS_POINTS - 1);
-          if (!(tq > lo_t && tq < hi_t)) tq = lo_t + span * (tid == 0 ? 0.5 : 0.75);
+          const float lo_t = (float)s_ls_state[0], lo_f = (float)s_ls_state[1], lo_h = (float)s_ls_state[2];
+          const float hi_t = (float)s_ls_state[3], hi_f = (float)s_ls_state[4], hi_h = (float)s_ls_state[5];
+          const float span = hi_t - lo_t;
+          if (tid == 0) tq = lo_h > 0.f ? lo_t - lo_f / lo_h : -1.f;
+          else if (tid == 1) tq = hi_h > 0.f ? hi_t - hi_f / hi_h : -1.f;
+          else tq = lo_t + span * (float)(tid - 1) * (1.f / (LS_POINTS - 1));
+          if (!(tq > lo_t && tq < hi_t)) tq = lo_t + span * (tid == 0 ? 0.5f : 0.75f);
         }
-        s_t[tid] = (float)tq;
+        s_t[tid] = tq;
       }
       __syncthreads();
       ++nsync;
-      if (!ls_round<VPT>(a, z, w, my_sid, s_tab, s_t, s_ls, s_res, s_i, ls_parity, stride)) {
+      double lsv = 0.0;
+      if (!ls_round<VPT>(a, z, w, my_sid, s_tab, s_t, s_rows, s_ls, s_res, s_i, ls_parity, stride,
+                         lsv)) {
         alive = false;
         break;
       }
       ls_parity ^= 1;
-      if (tid == 0) {
-        double lo_t = s_ls_state[0], lo_f = s_ls_state[1], lo_h = s_ls_state[2];
+      if (warp == 0) {
+        // lane p < 16 evaluates trial point p; the bracket moves to the
+        // largest point with phi' < 0 and the smallest with phi' > 0 inside
+        // it (ties: lowest point index); every lane ends with the same state
+        const unsigned FULL = 0xffffffffu;
+        if (r == 0) {  // the warps' phi'(0) and G(d) partials, in order
+          float g0 = 0.f, gdd = 0.f;
+          for (int q = 0; q < nwarp; ++q) {
+            g0 += ((const float *)s_sc)[q];
+            gdd += ((const float *)(s_sc + 16))[q];
+          }
+          phi0 = (double)g0;
+          cg1 = 2.0 * a.gamma * (double)gdd;
+        }
+        const int p = lane & (LS_POINTS - 1);
+        const bool in = lane < LS_POINTS;
+        const double tp = (double)s_t[p];
+        const double f = phi0 + __shfl_sync(FULL, lsv, p) + cg1 * tp;
+        const double h = __shfl_sync(FULL, lsv, p + LS_POINTS) + cg1;
+        double lo_t = s_ls_state[0], lo_f = r == 0 ? phi0 : s_ls_state[1], lo_h = s_ls_state[2];
         double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
         double t = -1.0;
-        for (int p = 0; p < LS_POINTS; ++p) {
-          const double tp = (double)s_t[p];
-          const double f = phi0 + s_res[p] + cg1 * tp, h = s_res[LS_POINTS + p] + cg1;
-          if (r == 0 && p == 0) lo_h = h;  // slope just right of 0 (first point's side pattern)
-          if (r == 0 && p == LS_POINTS - 1) {
-            if (f <= 0.0) { t = 1.0; break; }
-            if (hi_h < 0.0) { hi_f = f; hi_h = h; }
-          }
-          if (f == 0.0) { t = tp; break; }
-          if (f < 0.0 && tp > lo_t && tp < hi_t) { lo_t = tp; lo_f = f; lo_h = h; }
-          if (f > 0.0 && tp < hi_t && tp > lo_t) { hi_t = tp; hi_f = f; hi_h = h; }
+        if (r == 0 && !(phi0 < 0.0)) t = 0.0;  // not a descent direction
+        // an exact root among the points (round 0: before the full step t = 1)
+        const unsigned zero = __ballot_sync(FULL, in && f == 0.0 && (r > 0 || p < LS_POINTS - 1));
+        if (zero && t < 0.0) t = (double)s_t[__ffs(zero) - 1];
+        if (r == 0) {
+          lo_h = __shfl_sync(FULL, h, 0);  // slope just right of 0 (first point's side pattern)
+          const double f1 = __shfl_sync(FULL, f, LS_POINTS - 1), h1 = __shfl_sync(FULL, h, LS_POINTS - 1);
+          if (t < 0.0 && f1 <= 0.0) t = 1.0;
+          if (hi_h < 0.0) { hi_f = f1; hi_h = h1; }
         }
         if (t < 0.0) {
+          float key = (in && f < 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : -1.f;
+          int who = lane;
+          for (int o = 16; o; o >>= 1) {
+            const float k2 = __shfl_xor_sync(FULL, key, o);
+            const int w2 = __shfl_xor_sync(FULL, who, o);
+            if (k2 > key || (k2 == key && w2 < who)) { key = k2; who = w2; }
+          }
+          if (key >= 0.f) {
+            lo_t = __shfl_sync(FULL, tp, who);
+            lo_f = __shfl_sync(FULL, f, who);
+            lo_h = __shfl_sync(FULL, h, who);
+          }
+          key = (in && f > 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : 2.f;
+          who = lane;
+          for (int o = 16; o; o >>= 1) {
+            const float k2 = __shfl_xor_sync(FULL, key, o);
+            const int w2 = __shfl_xor_sync(FULL, who, o);
+            if (k2 < key || (k2 == key && w2 < who)) { key = k2; who = w2; }
+          }
+          if (key <= 1.f) {
+            hi_t = __shfl_sync(FULL, tp, who);
+            hi_f = __shfl_sync(FULL, f, who);
+            hi_h = __shfl_sync(FULL, h, who);
+          }
           const double span = hi_t - lo_t;
           const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
-          const double na = lo_h > 0.0 ? lo_t - lo_f / lo_h : -1.0;
-          const double nb = hi_h > 0.0 ? hi_t - hi_f / hi_h : -2.0;
+          // Newton steps from both ends (FP32: they only test agreement)
+          const float na = lo_h > 0.0 ? (float)lo_t - (float)lo_f / (float)lo_h : -1.f;
+          const float nb = hi_h > 0.0 ? (float)hi_t - (float)hi_f / (float)hi_h : -2.f;
           // both ends on one linear piece of phi' (their Newton steps agree): exact
-          if (!(span > 0.0) || fabs(na - nb) <= 1e-6 * fabs(tsec) || span <= 1e-7 * hi_t ||
+          if (!(span > 0.0) || fabsf(na - nb) <= 1e-6f * fabsf((float)tsec) || span <= 1e-7 * hi_t ||
               r == LS_ROUNDS - 1)
             t = tsec;
         }
-        s_ls_state[0] = lo_t; s_ls_state[1] = lo_f; s_ls_state[2] = lo_h;
-        s_ls_state[3] = hi_t; s_ls_state[4] = hi_f; s_ls_state[5] = hi_h;
-        if (t >= 0.0) { s_ls_state[6] = fmin(fmax(t, lo_t), 1.0); s_ls_state[7] = 1.0; }
+        if (lane == 0) {
+          s_ls_state[0] = lo_t; s_ls_state[1] = lo_f; s_ls_state[2] = lo_h;
+          s_ls_state[3] = hi_t; s_ls_state[4] = hi_f; s_ls_state[5] = hi_h;
+          if (t >= 0.0) { s_ls_state[6] = fmin(fmax(t, lo_t), 1.0); s_ls_state[7] = 1.0; }
+        }
       }
       __syncthreads();
     }
     if (!alive) break;
     const double t = s_ls_state[6] >= 0.0 ? s_ls_state[6] : s_ls_state[0];
-    if (timer) { unsigned long long c1 = vmat_globaltimer(); tL += c1 - c0; c0 = c1; }
+    if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[3] += c1 - s_clk[4]; s_clk[4] = c1; }
     if (t <= 0.0) { status = VMAT_ENOTCONV; break; }
 
     // ---------------- update
@@ -593,7 +699,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < VPT; ++v) z[v] = 0.f;
-#pragma unroll 4
+#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
   for (int q = 0; q < nnzs; ++q) {
     const int s = s_nz[q], mk = s_mask[s];
     const float *Ms = a.M + (size_t)s * a.Vpad;
@@ -614,7 +720,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     float zo[4], fo[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int v = 4 * m + q, id = my_sid[v];
+      const int v = 4 * m + q, id = sid_of(my_sid, v);
       fo[q] = vmat_dF(z[v], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
       zo[q] = z[v];
       cst += vmat_F((double)z[v], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
@@ -656,10 +762,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         if (a.rec_iters) *a.rec_iters = it;
         if (a.rec_status) *a.rec_status = status;
         if (a.stats) {
-          a.stats[0] += (double)tA;
-          a.stats[1] += (double)tS;
-          a.stats[2] += (double)tB;
-          a.stats[3] += (double)tL;
+          a.stats[0] += (double)s_clk[0];
+          a.stats[1] += (double)s_clk[1];
+          a.stats[2] += (double)s_clk[2];
+          a.stats[3] += (double)s_clk[3];
           a.stats[4] += (double)nsync;
           a.stats[5] += (double)it;
         }
@@ -671,7 +777,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 
 // ---------------------------------------------------------------- launch
 static size_t master_smem_bytes(int N, int nthr, int vpt) {
-  const size_t tile = (size_t)nthr * vpt, ng = vpt / 4;
+  const size_t ng = vpt / 4, tile = (size_t)nthr * (vpt + 33);  // F' tile + line-search rows
   return (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +
          (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + tile * 4 + (size_t)N * ng * 4 +
          (size_t)(8 + 4 * N + 1 + N * ng) * 4 + 16;
