@@ -397,7 +397,7 @@ def run_cpu_baseline(prob, args):
 def run_batched(args):
     """Sixteen independent plans of uneven size (seeds 10-25: 90-180 beams,
     40x40 or 60x40 MLC, prostate- or head-and-neck-like, 0.4-2.2 M voxels):
-    FP16-D plans in one tuned batch (lanes of concurrent plans, one CUDA graph
+    FP16-D plans in one tuned batch (per-plan SM budgets, plans side by side, one CUDA graph
     launch) against the plain FP32 single-plan loop on the same GPU."""
     import torch
     from paper_1005_4396_b300 import inputs, vmat
@@ -424,7 +424,7 @@ def run_batched(args):
         del prob
     t_setup = time.perf_counter() - t_setup
     batch = vmat.Batch(plans16)
-    lanes, trial = batch.tune(trial_iters=20, kkt_tol=kkt)
+    share, trial = batch.tune(trial_iters=20, kkt_tol=kkt)
     batch.run(kkt_tol=kkt)  # warm-up replay
     outs, plan_ms, total_ms = batch.run(kkt_tol=kkt)
     errs = []
@@ -444,7 +444,7 @@ def run_batched(args):
            "config": {"workload": f"{n} plans, seeds 10-25, grid voxels "
                                   f"{min(c.n_vox for c in cfgs)}-{max(c.n_vox for c in cfgs)}, "
                                   f"beams 90-180, MLC 40x40/60x40, scale {args.batch_scale}",
-                      "lanes": lanes, "tuner_trial_ms": trial},
+                      "sm_share": share, "tuner_trial_ms": trial},
            "batched_s": round(total_ms / 1e3, 3),
            "per_plan_wall_s": [round(v / 1e3, 3) for v in plan_ms],
            "fp32_single_plan_loop": {"plans_per_s": round(n / sum(fp32), 4),

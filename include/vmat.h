@@ -254,26 +254,41 @@ VMAT_API vmat_status vmat_smoothing_batch32(vmat_ctx *ctx, const float *Y_dev, d
 VMAT_API vmat_status vmat_set_master_budget(vmat_ctx *ctx, int32_t max_ctas);
 
 /* ---- many independent plans (planning throughput; not in the paper) ----
- * A batch groups existing contexts (not owned) into "lanes": each lane is a
- * stream that runs its plans one after another, and every plan's master
- * kernel is tiled for SMs/lanes CTAs so that lanes co-run.  The whole
- * multi-lane run (reset + all iterations of every plan) is captured once
- * into a CUDA graph and replayed with one launch.  While a plan belongs to a
- * batch its context runs on the batch's lane stream. */
+ * A batch groups existing contexts (not owned).  Every plan's master kernel
+ * gets a CTA budget (its SM "tokens"); a list schedule decides which plans
+ * run side by side, and each plan starts after the plans whose tokens it
+ * takes over, so plans that overlap always hold disjoint SMs.  The whole run
+ * (reset + all iterations of every plan) is captured once into a CUDA graph
+ * with those dependencies and replayed with one launch.  While a plan
+ * belongs to a batch its context runs on a stream of the batch. */
 typedef struct vmat_batch vmat_batch;
 VMAT_API vmat_status vmat_batch_create(vmat_ctx *const *plans, int32_t n_plans, void *cuda_stream,
                                        vmat_batch **out);
 VMAT_API void vmat_batch_destroy(vmat_batch *b);
 VMAT_API const char *vmat_batch_last_error(const vmat_batch *b);
-/* Use `lanes` concurrent lanes (1..min(plans, SMs)); plans are dealt to the
- * lane with the least estimated work (active voxels x beams), largest first.
- * VMAT_EINVAL if some plan's active voxels do not fit SMs/lanes CTAs. */
-VMAT_API vmat_status vmat_batch_configure(vmat_batch *b, int32_t lanes);
+/* SM share (1..SMs): plan p's master kernel gets max(SMs / share, the CTAs
+ * that keep it at <= 16 voxels per thread) CTAs, at most SMs.  Plans are
+ * placed largest estimated work (active voxels x beams per CTA) first, each
+ * on the SM tokens that free up earliest.  share = 1 runs the plans one after
+ * another on the whole GPU.  VMAT_EINVAL if share is out of range or a plan
+ * does not fit the GPU. */
+VMAT_API vmat_status vmat_batch_configure(vmat_batch *b, int32_t share);
 /* Autotuner: times a captured trial run of the first trial_iters iterations
- * of every plan for 1, 2, 4 and 8 lanes (ms_out [4], -1 where infeasible) and
- * configures the fastest (lanes_out). */
+ * of every plan for shares 1, 2, 3 and 4 (ms_out [4], -1 where not tried)
+ * and configures the fastest (share_out). */
 VMAT_API vmat_status vmat_batch_tune(vmat_batch *b, int32_t trial_iters, int32_t master_max_iters,
-                                     double kkt_tol, int32_t *lanes_out, double *ms_out);
+                                     double kkt_tol, int32_t *share_out, double *ms_out);
+/* The batch's list schedule, exposed for testing (host only, no GPU):
+ * n plans with CTA budgets budget [n] (1..sms) and estimated work est [n]
+ * (>= 0) on sms SM tokens.  Out: order [n] capture order (decreasing est,
+ * stable); ndep [n] and deps [n*n] (row p, first ndep[p] entries) the plans
+ * each plan must wait for; tokens [n*sms] (or NULL) 1 where plan p holds
+ * token t.  Any two plans holding a common token are ordered by the
+ * dependencies, so plans that may overlap hold disjoint tokens.
+ * VMAT_EINVAL on bad sizes. */
+VMAT_API vmat_status vmat_list_schedule(int32_t n, const int32_t *budget, const double *est,
+                                        int32_t sms, int32_t *order, int32_t *ndep, int32_t *deps,
+                                        uint8_t *tokens);
 /* Run every plan's full column generation (one aperture per beam) from an
  * empty plan as one graph launch.  res [n_plans] as for vmat_colgen_run
  * (phase_ms unused), plan_ms [n_plans] time from the launch to each plan's

@@ -1,14 +1,18 @@
 // Many independent plans at once.
 //
 // Planning throughput for a clinic runs many plans; a single plan's master
-// kernel leaves the GPU latency-bound (grid-wide reductions every iteration).
-// A batch runs plans concurrently in "lanes": each lane is a stream that runs
-// its plans one after another; the master kernel of each plan is re-tiled to a
-// budget of SMs / lanes CTAs, so the persistent master kernels of different
-// lanes co-run on disjoint SMs while the small kernels interleave.  The whole
-// multi-lane run (reset + every column-generation iteration of every plan) is
-// captured once into a CUDA graph and replayed with a single launch.  The lane
-// count is chosen by an autotuner that times short trial runs.
+// kernel leaves the GPU latency-bound (grid-wide reductions every iteration),
+// and a small plan runs about as fast on a third of the SMs as on all of them.
+// A batch gives every plan a CTA budget for its persistent master kernel:
+// SMs / share, raised where fewer CTAs would need more than 16 voxels per
+// thread.  The budgets are SM "tokens": a list schedule (largest estimated
+// work first, each plan on the tokens that free up earliest) decides which
+// plans run side by side, and each plan starts after the plans that held its
+// tokens before it.  Whatever the actual run times, plans that overlap hold
+// disjoint tokens, so their cooperative kernels are co-resident.  The whole
+// run (reset + every column-generation iteration of every plan) is captured
+// once into a CUDA graph with those dependencies and replayed with a single
+// launch.  The share is chosen by an autotuner that times short trial runs.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -18,11 +22,12 @@
 struct vmat_batch {
   std::vector<vmat_ctx *> plans;
   std::vector<cudaStream_t> orig;  // each plan's stream before the batch took it
-  std::vector<cudaStream_t> lane_st;
+  std::vector<cudaStream_t> plan_st;  // one capture stream per plan
   cudaStream_t user = nullptr;    // caller's stream: the batch starts after its prior work
   cudaStream_t origin = nullptr;  // the batch's own stream (capturable; the legacy stream is not)
-  int lanes = 0;
-  std::vector<std::vector<int>> lane_plans;
+  int share = 0;                      // configured SM share (0: not configured)
+  std::vector<int> order;             // capture order (list-schedule order)
+  std::vector<std::vector<int>> deps; // plans whose SM tokens each plan takes over
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int g_iters = -2, g_trial = -2;
@@ -30,7 +35,7 @@ struct vmat_batch {
   std::vector<Records> rec;
   char *rec_block = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_start = nullptr, ev_stop = nullptr;
-  std::vector<cudaEvent_t> ev_end, ev_join;
+  std::vector<cudaEvent_t> ev_end, ev_dep;
   std::string err;
 };
 
@@ -76,10 +81,15 @@ extern "C" vmat_status vmat_batch_create(vmat_ctx *const *plans, int32_t n, void
   for (vmat_ctx *c : b->plans) b->orig.push_back(c->stream);
   b->user = (cudaStream_t)cuda_stream;
   b->ev_end.resize(n, nullptr);
+  b->ev_dep.resize(n, nullptr);
+  b->plan_st.resize(n, nullptr);
   bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreate(&b->ev_fork) == cudaSuccess && cudaEventCreate(&b->ev_start) == cudaSuccess &&
             cudaEventCreate(&b->ev_stop) == cudaSuccess;
-  for (int p = 0; ok && p < n; ++p) ok = cudaEventCreate(&b->ev_end[p]) == cudaSuccess;
+  for (int p = 0; ok && p < n; ++p)
+    ok = cudaEventCreate(&b->ev_end[p]) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_dep[p], cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->plan_st[p], cudaStreamNonBlocking) == cudaSuccess;
   // device records: one block, per plan n_angles entries of each field
   size_t total = 0;
   for (vmat_ctx *c : b->plans) total += (size_t)c->N * (4 * 4 + 4 * 8) + 64;
@@ -110,13 +120,15 @@ extern "C" vmat_status vmat_batch_create(vmat_ctx *const *plans, int32_t n, void
 
 extern "C" void vmat_batch_destroy(vmat_batch *b) {
   if (!b) return;
-  for (cudaStream_t s : b->lane_st) cudaStreamSynchronize(s);
+  for (cudaStream_t s : b->plan_st)
+    if (s) cudaStreamSynchronize(s);
   drop_graph(b);
   for (size_t p = 0; p < b->plans.size(); ++p) b->plans[p]->stream = b->orig[p];
-  for (cudaStream_t s : b->lane_st) cudaStreamDestroy(s);
+  for (cudaStream_t s : b->plan_st)
+    if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->ev_end)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : b->ev_join)
+  for (cudaEvent_t e : b->ev_dep)
     if (e) cudaEventDestroy(e);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_start) cudaEventDestroy(b->ev_start);
@@ -129,72 +141,106 @@ extern "C" void vmat_batch_destroy(vmat_batch *b) {
   delete b;
 }
 
-// Lanes: plans sorted by estimated work (active voxels x beams), each given to
-// the lane with the least work so far; every plan's master gets SMs/lanes CTAs.
-extern "C" vmat_status vmat_batch_configure(vmat_batch *b, int32_t lanes) {
-  if (!b) return VMAT_EINVAL;
-  const int n = (int)b->plans.size();
-  const int sms = b->plans[0]->num_sms;
-  if (lanes < 1 || lanes > n || lanes > sms)
-    return bfail(b, VMAT_EINVAL, "lanes must be in [1, min(plans, SMs)]");
-  for (cudaStream_t s : b->lane_st) BCUDA(b, cudaStreamSynchronize(s));
-  for (size_t p = 0; p < b->plans.size(); ++p) BCUDA(b, cudaStreamSynchronize(b->plans[p]->stream));
-  drop_graph(b);
-  while ((int)b->lane_st.size() < lanes) {
-    cudaStream_t s;
-    BCUDA(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    b->lane_st.push_back(s);
-    cudaEvent_t e;
-    BCUDA(b, cudaEventCreate(&e));
-    b->ev_join.push_back(e);
+// List schedule of plans on SM tokens (host only): plans in order of
+// decreasing estimated work (stable), each on the budget[p] tokens that free
+// up earliest in the simulated schedule (ties: lowest token), starting after
+// the last holders of those tokens, which become its dependencies.
+extern "C" vmat_status vmat_list_schedule(int32_t n, const int32_t *budget, const double *est,
+                                          int32_t sms, int32_t *order, int32_t *ndep,
+                                          int32_t *deps, uint8_t *tokens) {
+  if (n <= 0 || sms <= 0 || !budget || !est || !order || !ndep || !deps) return VMAT_EINVAL;
+  for (int p = 0; p < n; ++p)
+    if (budget[p] < 1 || budget[p] > sms || !(est[p] >= 0.0)) return VMAT_EINVAL;
+  std::vector<int> ord(n);
+  for (int p = 0; p < n; ++p) ord[p] = p;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return est[x] > est[y]; });
+  std::vector<double> free_at(sms, 0.0);
+  std::vector<int> holder(sms, -1), tok(sms);
+  if (tokens) std::fill(tokens, tokens + (size_t)n * sms, (uint8_t)0);
+  for (int i = 0; i < n; ++i) {
+    const int p = ord[i];
+    order[i] = p;
+    for (int t = 0; t < sms; ++t) tok[t] = t;
+    std::stable_sort(tok.begin(), tok.end(), [&](int x, int y) { return free_at[x] < free_at[y]; });
+    double start = 0.0;
+    for (int j = 0; j < budget[p]; ++j) start = std::max(start, free_at[tok[j]]);
+    int nd = 0;
+    for (int j = 0; j < budget[p]; ++j) {
+      const int t = tok[j];
+      const int h = holder[t];
+      if (h >= 0 && std::find(deps + (size_t)p * n, deps + (size_t)p * n + nd, h) == deps + (size_t)p * n + nd)
+        deps[(size_t)p * n + nd++] = h;
+      holder[t] = p;
+      free_at[t] = start + est[p];
+      if (tokens) tokens[(size_t)p * sms + t] = 1;
+    }
+    ndep[p] = nd;
   }
-  const int budget = sms / lanes;
-  for (vmat_ctx *c : b->plans) {
-    vmat_status s = vmat_reset(c);
-    if (s == VMAT_OK) s = vmat_set_master_budget(c, budget);
-    if (s != VMAT_OK) return bfail(b, s, std::string("plan reconfiguration: ") + c->err);
-  }
-  std::vector<int> order(n);
-  for (int p = 0; p < n; ++p) order[p] = p;
-  auto work = [&](int p) { return (double)b->plans[p]->Va * b->plans[p]->N; };
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
-  b->lane_plans.assign(lanes, {});
-  std::vector<double> load(lanes, 0.0);
-  for (int p : order) {
-    int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    b->lane_plans[l].push_back(p);
-    load[l] += work(p);
-  }
-  for (int l = 0; l < lanes; ++l)
-    for (int p : b->lane_plans[l]) b->plans[p]->stream = b->lane_st[l];
-  b->lanes = lanes;
   return VMAT_OK;
 }
 
-// Capture every lane's plans (reset + iterations) into one graph.
+// Budgets and list schedule for an SM share: plan p gets
+// b_p = max(SMs / share, CTAs for <= 16 voxels per thread at 512 threads)
+// tokens; plans are placed largest estimated work (active voxels x beams per
+// token) first, each on the b_p tokens that free up earliest (ties: lowest
+// token), after the last holders of those tokens.
+extern "C" vmat_status vmat_batch_configure(vmat_batch *b, int32_t share) {
+  if (!b) return VMAT_EINVAL;
+  const int n = (int)b->plans.size();
+  const int sms = b->plans[0]->num_sms;
+  if (share < 1 || share > sms) return bfail(b, VMAT_EINVAL, "share must be in [1, SMs]");
+  for (size_t p = 0; p < b->plans.size(); ++p) BCUDA(b, cudaStreamSynchronize(b->plans[p]->stream));
+  drop_graph(b);
+  std::vector<int32_t> bud(n);
+  std::vector<double> est(n);
+  for (int p = 0; p < n; ++p) {
+    vmat_ctx *c = b->plans[p];
+    const int64_t need = (c->Va + 16 * 512 - 1) / (16 * 512);
+    bud[p] = (int)std::min<int64_t>(sms, std::max<int64_t>(sms / share, need));
+    vmat_status s = vmat_reset(c);
+    if (s == VMAT_OK) s = vmat_set_master_budget(c, bud[p]);
+    if (s != VMAT_OK) return bfail(b, s, std::string("plan reconfiguration: ") + c->err);
+    est[p] = (double)c->Va * c->N / bud[p];
+  }
+  std::vector<int32_t> order(n), ndep(n), deps((size_t)n * n);
+  vmat_status ls = vmat_list_schedule(n, bud.data(), est.data(), sms, order.data(), ndep.data(),
+                                      deps.data(), nullptr);
+  if (ls != VMAT_OK) return bfail(b, ls, "list schedule");
+  b->deps.assign(n, {});
+  for (int p = 0; p < n; ++p) b->deps[p].assign(deps.begin() + (size_t)p * n, deps.begin() + (size_t)p * n + ndep[p]);
+  b->order.assign(order.begin(), order.end());
+  for (int p = 0; p < n; ++p) b->plans[p]->stream = b->plan_st[p];
+  b->share = share;
+  return VMAT_OK;
+}
+
+// Capture every plan (reset + iterations) into one graph: each plan on its
+// own stream, after the fork and after the plans whose tokens it takes over.
 static vmat_status build_graph(vmat_batch *b, int trial, int master_max_iters, double kkt) {
   drop_graph(b);
   cudaStream_t o = b->origin;
   BCUDA(b, cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed));
   vmat_status st = VMAT_OK;
   cudaError_t ce = cudaEventRecord(b->ev_fork, o);
-  for (int l = 0; l < b->lanes && ce == cudaSuccess; ++l) ce = cudaStreamWaitEvent(b->lane_st[l], b->ev_fork, 0);
-  for (int l = 0; l < b->lanes && ce == cudaSuccess && st == VMAT_OK; ++l) {
-    for (int p : b->lane_plans[l]) {
-      vmat_ctx *c = b->plans[p];
-      st = vmat_enqueue_reset(c);
-      const int n = trial > 0 ? std::min(trial, c->N) : c->N;
-      if (st == VMAT_OK) st = vmat_enqueue_colgen(c, n, master_max_iters, kkt, b->rec[p], true);
-      if (st != VMAT_OK) {
-        b->err = std::string("capture of plan ") + std::to_string(p) + ": " + c->err;
-        break;
-      }
-      ce = cudaEventRecordWithFlags(b->ev_end[p], b->lane_st[l], cudaEventRecordExternal);
-      if (ce != cudaSuccess) break;
+  for (size_t i = 0; i < b->order.size() && ce == cudaSuccess && st == VMAT_OK; ++i) {
+    const int p = b->order[i];
+    vmat_ctx *c = b->plans[p];
+    ce = cudaStreamWaitEvent(c->stream, b->ev_fork, 0);
+    for (size_t q = 0; q < b->deps[p].size() && ce == cudaSuccess; ++q)
+      ce = cudaStreamWaitEvent(c->stream, b->ev_dep[b->deps[p][q]], 0);
+    if (ce != cudaSuccess) break;
+    st = vmat_enqueue_reset(c);
+    const int n = trial > 0 ? std::min(trial, c->N) : c->N;
+    if (st == VMAT_OK) st = vmat_enqueue_colgen(c, n, master_max_iters, kkt, b->rec[p], true);
+    if (st != VMAT_OK) {
+      b->err = std::string("capture of plan ") + std::to_string(p) + ": " + c->err;
+      break;
     }
-    if (ce == cudaSuccess && st == VMAT_OK) ce = cudaEventRecord(b->ev_join[l], b->lane_st[l]);
-    if (ce == cudaSuccess && st == VMAT_OK) ce = cudaStreamWaitEvent(o, b->ev_join[l], 0);
+    ce = cudaEventRecordWithFlags(b->ev_end[p], c->stream, cudaEventRecordExternal);
+    if (ce == cudaSuccess) ce = cudaEventRecord(b->ev_dep[p], c->stream);
   }
+  for (size_t p = 0; p < b->plans.size() && ce == cudaSuccess && st == VMAT_OK; ++p)
+    ce = cudaStreamWaitEvent(o, b->ev_dep[p], 0);  // join every plan stream
   cudaGraph_t g = nullptr;
   cudaError_t ec = cudaStreamEndCapture(o, &g);
   if (st != VMAT_OK || ce != cudaSuccess || ec != cudaSuccess) {
@@ -234,16 +280,16 @@ static vmat_status launch_graph(vmat_batch *b, double *total_ms) {
 }
 
 extern "C" vmat_status vmat_batch_tune(vmat_batch *b, int32_t trial_iters, int32_t master_max_iters,
-                                       double kkt_tol, int32_t *lanes_out, double *ms_out) {
+                                       double kkt_tol, int32_t *share_out, double *ms_out) {
   if (!b || trial_iters <= 0) return b ? bfail(b, VMAT_EINVAL, "trial_iters must be > 0") : VMAT_EINVAL;
-  const int cand[4] = {1, 2, 4, 8};
+  const int cand[4] = {1, 2, 3, 4};
   int best = -1;
   double best_ms = 0.0;
   for (int q = 0; q < 4; ++q) {
     if (ms_out) ms_out[q] = -1.0;
-    const int lanes = cand[q];
-    if (lanes > (int)b->plans.size() || lanes > b->plans[0]->num_sms) continue;
-    if (vmat_batch_configure(b, lanes) != VMAT_OK) continue;  // a plan does not fit the budget
+    const int share = cand[q];
+    if (share > (int)b->plans.size() || share > b->plans[0]->num_sms) continue;
+    if (vmat_batch_configure(b, share) != VMAT_OK) continue;
     vmat_status s = build_graph(b, trial_iters, master_max_iters, kkt_tol);
     double ms = 0.0;
     if (s == VMAT_OK) s = launch_graph(b, nullptr);  // first replay: warm-up
@@ -251,14 +297,14 @@ extern "C" vmat_status vmat_batch_tune(vmat_batch *b, int32_t trial_iters, int32
     if (s != VMAT_OK) return s;
     if (ms_out) ms_out[q] = ms;
     if (best < 0 || ms < best_ms) {
-      best = lanes;
+      best = share;
       best_ms = ms;
     }
   }
-  if (best < 0) return bfail(b, VMAT_EINVAL, "no lane count fits every plan");
+  if (best < 0) return bfail(b, VMAT_EINVAL, "no SM share fits every plan");
   vmat_status s = vmat_batch_configure(b, best);
   if (s != VMAT_OK) return s;
-  if (lanes_out) *lanes_out = best;
+  if (share_out) *share_out = best;
   return VMAT_OK;
 }
 
@@ -268,7 +314,7 @@ extern "C" vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_i
   if (!b) return VMAT_EINVAL;
   if (master_max_iters < 0 || !(kkt_tol >= 0.0))
     return bfail(b, VMAT_EINVAL, "master_max_iters >= 0 and kkt_tol >= 0 required");
-  if (b->lanes == 0) {
+  if (b->share == 0) {
     vmat_status s = vmat_batch_configure(b, 1);
     if (s != VMAT_OK) return s;
   }

@@ -96,6 +96,7 @@ EXPORTS = {
     "vmat_batch_configure": [_p, _i32],
     "vmat_batch_tune": [_p, _i32, _i32, _d, _p, _p],
     "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
+    "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
 }
 
 _lib = None
@@ -425,9 +426,28 @@ def _result_arrays(N, R, n):
     return out, res
 
 
+def vmat_list_schedule(budget, est, sms, want_tokens=False):
+    """The batch's list schedule (host only): returns (order, deps, tokens)
+    with deps[p] the plans plan p waits for and tokens [n, sms] bool or None."""
+    budget = np.ascontiguousarray(budget, dtype=np.int32)
+    est = np.ascontiguousarray(est, dtype=np.float64)
+    n = budget.size
+    order = np.zeros(n, np.int32)
+    ndep = np.zeros(n, np.int32)
+    deps = np.zeros(n * n, np.int32)
+    tokens = np.zeros(n * sms, np.uint8) if want_tokens else None
+    st = load_library().vmat_list_schedule(n, _ptr(budget), _ptr(est), int(sms), _ptr(order),
+                                           _ptr(ndep), _ptr(deps), _ptr(tokens))
+    if st != VMAT_OK:
+        raise VmatError(st, "vmat_list_schedule: bad sizes")
+    dl = [deps[p * n:p * n + ndep[p]].tolist() for p in range(n)]
+    return order, dl, (tokens.reshape(n, sms).astype(bool) if want_tokens else None)
+
+
 class Batch:
-    """Many plans at once: lanes of concurrent plans, one CUDA graph per run.
-    While a Plan is in a batch its context runs on the batch's lane stream."""
+    """Many plans at once: per-plan SM budgets, a list schedule of which plans
+    run side by side, one CUDA graph per run.  While a Plan is in a batch its
+    context runs on a stream of the batch."""
 
     def __init__(self, plans):
         import torch
@@ -447,16 +467,16 @@ class Batch:
             raise VmatError(st, load_library().vmat_batch_last_error(self.h).decode())
         return st
 
-    def configure(self, lanes):
-        self._chk(load_library().vmat_batch_configure(self.h, int(lanes)))
+    def configure(self, share):
+        self._chk(load_library().vmat_batch_configure(self.h, int(share)))
 
     def tune(self, trial_iters=20, master_max_iters=100000, kkt_tol=1e-6):
-        lanes = ctypes.c_int32()
+        share = ctypes.c_int32()
         ms = np.zeros(4)
         self._chk(load_library().vmat_batch_tune(self.h, int(trial_iters), int(master_max_iters),
-                                                 float(kkt_tol), ctypes.byref(lanes),
+                                                 float(kkt_tol), ctypes.byref(share),
                                                  ms.ctypes.data))
-        return lanes.value, dict(zip((1, 2, 4, 8), ms.tolist()))
+        return share.value, dict(zip((1, 2, 3, 4), ms.tolist()))
 
     def run(self, master_max_iters=100000, kkt_tol=1e-6):
         outs, ress = [], []

@@ -52,7 +52,7 @@ def test_fluence_cost_and_gradient_match_oracle(small, small_plan):
     g = X.grad.cpu().numpy()
     for b in (0, 9, 31):
         x = Xh[:, b].astype(np.float64)
-        assert float(cost[b]) == pytest.approx(_oracle_cost(prob, x), rel=1e-5)
+        assert float(cost[b].detach()) == pytest.approx(_oracle_cost(prob, x), rel=1e-5)
         assert _rel(g[:, b], w[b] * _oracle_grad_x(prob, x)) <= 1e-4
 
 
