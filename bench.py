@@ -34,7 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
-MASTER_TRAFFIC_RATIO = (8.186832e9 + 10.338048e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
+# DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
+# current kernel (bench.py --case master: 8.224058 GB read + 7.762 MB written
+# for (2*30+2) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
+# to None whenever the kernel changes until it has been captured again
+MASTER_TRAFFIC_RATIO = (8.224058e9 + 7.762176e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 
@@ -170,6 +174,7 @@ def run_ours(args):
     cfg = _workload(args.workload)
     prob = inputs.make_problem(cfg)
     plan = vmat.Plan(prob, val_f32=True)
+    plan.set_master_method(args.master)
     info = plan.info
     plan.set_profiling(True)
 
@@ -225,9 +230,10 @@ def run_ours(args):
         "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4) if dom_gbs else None,
         "peak_kind": f"{peak_kind} copy bandwidth",
         # DRAM bytes per launch = measured traffic/algorithmic ratio of one ncu capture of
-        # this kernel (half-depth phantom, 150 columns, 30 iterations: 8.197 GB read+write
-        # for 8.239 GB algorithmic) times this launch's algorithmic bytes
-        "traffic": round(MASTER_TRAFFIC_RATIO * float(mb.sum()) / n_master, 0) if dom == 3 else None,
+        # this kernel (half-depth phantom, 150 columns, 30 iterations) times this launch's
+        # algorithmic bytes
+        "traffic": (round(MASTER_TRAFFIC_RATIO * float(mb.sum()) / n_master, 0)
+                    if dom == 3 and MASTER_TRAFFIC_RATIO else None),
         "traffic_note": "per launch (average over the plan), scaled from one ncu capture of a "
                         "smaller case; see profiles/k_master_halfdepth_150cols.md",
         "launches_per_step": n_master,
@@ -271,18 +277,24 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded phantom and ray/Gaussian D; no clinical data)",
            "config": {"workload": _describe(cfg, prob), "parallelism": f"replicas x{ws}",
-                      "l2": "inputs larger than L2 (D 3.6 GB per copy, aperture-dose matrix up to "
-                            f"{info['n_active'] * cfg.n_angles * 4 / 1e6:.0f} MB); no flush",
+                      "l2": (f"D {prob.nnz * 8 / 1e9:.2f} GB per copy (FP32 value + int32 index), "
+                             f"aperture-dose matrix up to {info['n_active'] * cfg.n_angles * 4 / 1e6:.0f} MB; "
+                             + ("inputs larger than L2 (126 MB); no flush" if prob.nnz * 8 > 126e6 else
+                                "the tiny workload fits in L2; no flush (L2-resident by design)")),
                       "active_voxels": info["n_active"],
                       "master_launch": [info["master_grid"], info["master_block"]]},
            "gpu_launches": int(launches),
            "roofline": roofline, "spmv": spmv,
            "phases_ms_per_plan": {n: round(float(v), 3) for n, v in zip(names, ph_tot)},
-           "pg_iters_per_plan": int(np.mean([r["iters"].sum() for r in recs])),
+           "master_method": {"pg": "projected gradient (Sec. 2.2)",
+                             "newton": "projected Newton (option beyond the paper)"}[args.master],
+           "master_iters_per_plan": int(np.mean([r["iters"].sum() for r in recs])),
            "final_cost": float(recs[-1]["cost"][-1]),
            "clocks": clocks}
 
     if rank == 0 and ws == 1 and not args.quick:
+        if args.master == "pg":
+            out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
         out["variants"] = run_variants(prob, plan, recs[-1], kkt)
         out["e2e"] = run_e2e(prob, args)
         out["cpu_baseline"] = run_cpu_baseline(prob, args)
@@ -291,6 +303,46 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_newton(prob, plan, rec_pg, kkt, args):
+    """The same plan with the projected-Newton master (an option beyond the
+    paper): CG iterations/s, master iterations and where the time goes; its
+    plan's dose against the FP64 oracle for the same apertures and
+    intensities."""
+    import torch
+    plan.set_master_method("newton")
+    try:
+        for _ in range(args.warmup):
+            plan.reset()
+            plan.colgen_run(kkt_tol=kkt)
+        recs = []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.steps):
+            plan.reset()
+            recs.append(plan.colgen_run(kkt_tol=kkt))
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        r = recs[-1]
+        ph = np.sum([q["phase_ms"] for q in recs], axis=0).sum(axis=0) / args.steps
+        z = plan.plan_dose().cpu().numpy()
+        emax, _ = _dose_err(prob, plan, z, r["lleaf"], r["rleaf"], r["y"])
+    finally:
+        plan.set_master_method("pg")
+    n = len(r["k"])
+    return {"value": round(n / (ms / 1e3), 3), "unit": UNIT, "ms_per_plan": round(ms, 3),
+            "master_iters_per_plan": int(np.mean([q["iters"].sum() for q in recs])),
+            "max_master_iters": int(r["iters"].max()),
+            "phases_ms_per_plan": {k: round(float(v), 3) for k, v in
+                                   zip(["price_spmv", "pricing", "aperture", "master"], ph)},
+            "final_cost": float(r["cost"][-1]), "final_cost_pg": float(rec_pg["cost"][-1]),
+            "beams_in_same_order_as_pg": int(np.sum(r["k"] == rec_pg["k"])),
+            "max_dose_err_pct_rx": round(emax, 6),
+            "note": "same workload and KKT rule; not the paper's method (Sec. 2.2 names the gradient "
+                    "projection method), so not the headline value"}
 
 
 def run_variants(prob, plan32, rec32, kkt=1e-6):
@@ -410,6 +462,7 @@ def run_batched(args):
         prob = inputs.make_problem(c)
         # plain FP32 single-plan loop: whole plan on the whole GPU
         with vmat.Plan(prob, val_f32=True) as p32:
+            p32.set_master_method(args.master)
             p32.colgen_run(kkt_tol=kkt)  # warm-up
             p32.reset()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -419,6 +472,7 @@ def run_batched(args):
             torch.cuda.synchronize()
             fp32.append(a.elapsed_time(b) / 1e3)
         p16 = vmat.Plan(prob, dtype="f16", val_f32=True)
+        p16.set_master_method(args.master)
         plans16.append(p16)
         probs.append(prob if len(probs) < 3 else None)  # keep a few for the dose check
         del prob
@@ -439,6 +493,7 @@ def run_batched(args):
     n = len(plans16)
     iters = sum(c.n_angles for c in cfgs)
     out = {"metric": "plans/s (FP16-D batched, one graph launch) vs FP32 single-plan loop",
+           "master_method": args.master,
            "value": round(n / (total_ms / 1e3), 4), "unit": "plans/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "f16-D, f32 accumulate", "data": "synthetic",
            "config": {"workload": f"{n} plans, seeds 10-25, grid voxels "
@@ -455,6 +510,84 @@ def run_batched(args):
     batch.close()
     for p in plans16:
         p.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_autograd(args):
+    """Differentiable dose + cost on the prostate phantom: 32 fluence vectors
+    per call (U(0,1), 288,000 beamlets) forward + hand-written backward, and
+    32 aperture-intensity vectors through random deliverable-shaped apertures;
+    throughput in vectors/s with CUDA events, and sampled errors against the
+    FP64 oracle gradient and central differences of the oracle cost
+    (h = 1e-3, 8 directions normalised to |d|_inf = 1)."""
+    import torch
+    from paper_1005_4396_b300 import autograd, inputs, vmat
+    import oracle
+    torch.cuda.set_device(0)
+    prob = inputs.make_problem(inputs.prostate_config())
+    cfg = prob.cfg
+    sid, T, al, be = prob.struct_id, prob.T, prob.alpha, prob.beta
+
+    def ocost(x):
+        return oracle.voxel_cost(oracle.dose(prob, x), sid, T, al, be)
+
+    def ograd(x):
+        return oracle.price(prob, oracle.voxel_dcost(oracle.dose(prob, x), sid, T, al, be))
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    out = {"metric": "differentiable dose+cost: fluence vectors/s (forward + backward, 32 per call)",
+           "unit": "vectors/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": _describe(cfg, prob), "batch": 32}}
+    with vmat.Plan(prob, val_f32=True) as plan:
+        Xh = inputs.fluence_batch(91, prob.n_beamlets, 32).T.copy()
+        X = torch.tensor(Xh, device="cuda", requires_grad=True)
+        l, r = inputs.random_apertures(92, cfg)
+        ld, rd = torch.tensor(l, device="cuda"), torch.tensor(r, device="cuda")
+        Yh = inputs.rng.uniform(93, cfg.n_angles * 32).astype(np.float32).reshape(cfg.n_angles, 32)
+        Y = torch.tensor(Yh, device="cuda", requires_grad=True)
+
+        def step_x():
+            X.grad = None
+            autograd.dose_cost(plan, X).sum().backward()
+
+        def step_y():
+            Y.grad = None
+            autograd.aperture_dose_cost(plan, Y, ld, rd).sum().backward()
+
+        for name, fn in (("fluence", step_x), ("intensity", step_y)):
+            for _ in range(max(args.warmup, 3)):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(args.steps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / args.steps
+            out[name] = {"ms_per_call": round(ms, 3), "vectors_per_s": round(32 / (ms / 1e3), 1)}
+        out["value"] = out["fluence"]["vectors_per_s"]
+        # errors on sampled vectors
+        step_x()
+        gx = X.grad.cpu().numpy()
+        x = Xh[:, 5].astype(np.float64)
+        out["fluence"]["rel_err_vs_oracle_grad"] = rel(gx[:, 5], ograd(x))
+        dirs = inputs.rng.normal(94, 8 * prob.n_beamlets).reshape(8, prob.n_beamlets)
+        dirs /= np.abs(dirs).max(axis=1, keepdims=True)
+        h = 1e-3
+        fd = np.array([(ocost(x + h * d) - ocost(x - h * d)) / (2 * h) for d in dirs])
+        out["fluence"]["rel_err_vs_central_differences"] = rel(dirs @ gx[:, 5].astype(np.float64), fd)
+        step_y()
+        gy = Y.grad.cpu().numpy()
+        y = Yh[:, 2].astype(np.float64)
+        xf = oracle.aperture_fluence(cfg, l, r, y)
+        g_or = oracle.aperture_adjoint(cfg, l, r, ograd(xf)) + \
+            cfg.gamma * oracle.dG(prob.theta_deg, y, cfg.cyclic)
+        out["intensity"]["rel_err_vs_oracle_grad"] = rel(gy[:, 2], g_or)
+    out["note"] = ("one call = forward dose+cost of 32 vectors and the backward of their sum; "
+                   "errors: relative 2-norm on one sampled vector")
     print(json.dumps(out), flush=True)
 
 
@@ -538,7 +671,14 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the sixteen-plan batch (FP16-D, graph) against the FP32 single-plan loop")
     ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--master", default="pg", choices=["pg", "newton"],
+                    help="master method of the timed plan (pg: the paper's gradient projection)")
+    ap.add_argument("--autograd", action="store_true",
+                    help="the differentiable dose+cost (32 vectors per call) on the prostate phantom")
     args = ap.parse_args()
+    if args.autograd:
+        run_autograd(args)
+        return
     if args.case:
         run_case(args)
         return

@@ -58,6 +58,8 @@ struct MasterArgs {
   float *z_out, *fp_out;  // [Vpad]
   MasterOut *out;
   double *stats;         // [8] cumulative: ns in pass A+reduce, step, pass B, search; syncs; iters
+  float *hpart;          // projected Newton: [grid][(N+1)(N+2)/2] per-CTA Gram partials
+  float *hred;           // projected Newton: [(N+1)(N+2)/2] their sum (packed lower triangle)
   double *rec_cost, *rec_rho;
   int32_t *rec_iters, *rec_status;
   double inactive_cost;
@@ -271,7 +273,60 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
   return true;
 }
 
-template <int VPT>
+// Floats of the region holding the line-search rows ([nthr][33]); the
+// projected-Newton variant also stages its Gram chunks ([64][N+8]) and its
+// packed factor ((N+1)(N+2)/2) there.  A multiple of 4 (keeps what follows
+// 16-byte aligned).
+__host__ __device__ __forceinline__ int master_rows_len(int N, int nthr, bool newton) {
+  int r = 33 * nthr;
+  if (newton) {
+    const int st = 64 * (N + 8), fac = (N + 1) * (N + 2) / 2;
+    r = max(r, max(st, fac));
+  }
+  return (r + 3) & ~3;
+}
+
+// ---------------------------------------------------------------- projected Newton
+// Packed lower triangle: entry (i, j), j <= i, at i(i+1)/2 + j.
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Cholesky of the n x n leading block of the packed (n+1) x (n+1) matrix A
+// whose last row holds a right-hand side b: afterwards A's rows 0..n-1 hold
+// L below the diagonal (diagonal in dg), and row n holds y with L y = b (the
+// forward substitution rides along).  Right-looking, one CTA barrier per
+// pivot; the pivot column travels in a double-buffered copy (cb) so that the
+// next column is gathered by the threads that update it.  Returns false in
+// every thread if a pivot is not positive.
+__device__ bool chol_packed_aug(float *A, int n, float *cb, float *dg) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5,
+            nwarp = nthr >> 5;
+  for (int i = tid; i <= n; i += nthr) cb[i] = A[pk(i, 0)];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float *c = cb + (k & 1) * (n + 1);
+    float *cn = cb + ((k + 1) & 1) * (n + 1);
+    const float d = c[k];
+    if (!(d > 0.f) || !isfinite(d)) return false;
+    const float sq = sqrtf(d), isq = 1.f / sq, inv = 1.f / d;
+    if (tid == 0) dg[k] = sq;
+    for (int i = k + 1 + warp; i <= n; i += nwarp) {
+      const float ci = c[i];
+      if (lane == 0) A[pk(i, k)] = ci * isq;
+      const float f = -ci * inv;
+      const int jmax = i < n - 1 ? i : n - 1;
+      float *row = A + pk(i, 0);
+      for (int j = k + 1 + lane; j <= jmax; j += 32) {
+        const float v = fmaf(f, c[j], row[j]);
+        row[j] = v;
+        if (j == k + 1) cn[i] = v;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+template <int VPT, bool NEWTON>
 __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ns = a.nslots, tid = threadIdx.x, nthr = blockDim.x;
@@ -298,15 +353,30 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   float *s_tab = s_df + N;                        // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
   float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
-  float *s_fp = s_ls + 16 * 32;                   // [NG][ST] F' of the CTA's subtiles (pass A)
+  // 16-byte aligned for float4 access (the sizes above leave 8-byte alignment when N is odd)
+  float *s_fp = (float *)(((uintptr_t)(s_ls + 16 * 32) + 15) & ~(uintptr_t)15);  // [NG][ST] F' (pass A)
   float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
-  float *s_pp = s_rows + 33 * nthr;               // [N*NG] warp partial per (slot, subtile) pair
+  const int rows_len = master_rows_len(N, nthr, NEWTON);
+  float *s_pp = s_rows + rows_len;                // [N*NG] warp partial per (slot, subtile) pair
   int *s_i = (int *)(s_pp + N * NG);              // [8]: 1 nonzero slots, 2 nonzero pairs
   int *s_beam = s_i + 8;                          // [N] beam of slot
   int *s_nz = s_beam + N;                         // [N] slots with a nonzero subtile here
   int *s_mask = s_nz + N;                         // [N] per slot: bit m = subtile m nonzero
   int *s_pst = s_mask + N;                        // [N+1] first pair of each slot
   int *s_pair = s_pst + N + 1;                    // [N*NG] pairs s*8+m in slot order
+  // projected Newton only (the launch sizes these for that variant)
+  int *s_fidx = s_pair + N * NG;                  // [N] free slots F, in slot order
+  int *s_sub = s_fidx + N;                        // [N] F positions kept after dropping blocked ones
+  int *s_ncol = s_sub + N;                        // [8] free columns nonzero in each own subtile
+  int *s_cols = s_ncol + 8;                       // [NG][N] their F positions
+  float *s_x = (float *)(s_cols + NG * N);        // [N] Newton step on F'
+  float *s_dg = s_x + N;                          // [N] diagonal of the Cholesky factor
+  float *s_cb = s_dg + N;                         // [2][N+1] pivot-column buffers
+  // idle while the Newton step is formed, so aliased: sqrt(c_j) of the own
+  // voxels on the F' tile, the staged Gram chunks and then the packed factor
+  // on the line-search rows (which are zeroed again afterwards)
+  float *s_sq = s_fp;                             // [NG][ST]
+  float *s_A = s_rows;                            // [max(64 (N+8), (N+1)(N+2)/2)]
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
   for (int q = tid; q < 33 * nthr; q += nthr) s_rows[q] = 0.f;
@@ -506,13 +576,243 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       else
         step = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
       step = fmin(fmax(step, 1e-12), 1e12);
+      bool newton_ok = false;
+      if (NEWTON) {
+        // ---- projected Newton: the Hessian of Eq. 3 on the free set
+        // F = {y > 0 or g < 0} is M_F^T C M_F + 2 gamma L_FF (C = 2 alpha_j or
+        // 2 beta_j by side, L the Laplacian of G); each CTA forms its voxels'
+        // part of the Gram matrix of A = M_F sqrt(C), the CTAs' parts are
+        // summed in a fixed order, and every CTA solves the same system.
+        const int HPM = (N + 1) * (N + 2) / 2;
+        if (tid == 0) {
+          int nf = 0;
+          for (int s = 0; s < ns; ++s)
+            if (s_y[s_beam[s]] > 0.0 || s_g[s] < 0.0) s_fidx[nf++] = s;
+          s_i[3] = nf;
+          for (int m = 0; m < NG; ++m) {
+            int c = 0;
+            for (int q = 0; q < nf; ++q)
+              if (s_mask[s_fidx[q]] >> m & 1) s_cols[m * N + c++] = q;
+            s_ncol[m] = c;
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < NG; ++m)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int v = 4 * m + q, id = sid_of(my_sid, v);
+            const float e = z[v] - s_tab[id];
+            s_sq[m * ST + 4 * tid + q] = sqrtf(2.f * (e > 0.f ? s_tab[512 + id] : s_tab[256 + id]));
+          }
+        __syncthreads();
+        const int nf = s_i[3];
+        if (nf > 0) {
+          float *hp = a.hpart + (size_t)blockIdx.x * HPM;
+          for (int q = tid; q < nf * (nf + 1) / 2; q += nthr) hp[q] = 0.f;
+          for (int m = 0; m < NG; ++m) {
+            const int nm = s_ncol[m];
+            if (nm == 0) continue;
+            const int P = (nm + 3) >> 2, ldA = 4 * P + 4, nblk = P * (P + 1) / 2;
+            const int *cols = s_cols + m * N;
+            for (int blk0 = 0; blk0 < nblk; blk0 += nthr) {
+              const int blk = blk0 + tid;
+              int bi = 0, bj = 0;
+              if (blk < nblk) {  // block (bi <= bj) of the upper triangle, row-major
+                int r = 0, rem = blk;
+                while (rem >= P - r) { rem -= P - r; ++r; }
+                bi = r;
+                bj = r + rem;
+              }
+              float acc[4][4];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = 0.f;
+              for (int v0 = 0; v0 < ST; v0 += 64) {
+                __syncthreads();
+                for (int idx = tid; idx < 4 * P * 64; idx += nthr) {  // chunk of A^T: [voxel][column]
+                  const int row = idx >> 6, v = idx & 63;
+                  float val = 0.f;
+                  if (row < nm)
+                    val = __ldg(a.M + (size_t)s_fidx[cols[row]] * a.Vpad + SUB_OFF(m) + v0 + v) *
+                          s_sq[m * ST + v0 + v];
+                  s_A[v * ldA + row] = val;
+                }
+                __syncthreads();
+                if (blk < nblk) {
+#pragma unroll 4
+                  for (int v = 0; v < 64; ++v) {
+                    const float4 xa = *(const float4 *)(s_A + v * ldA + 4 * bi);
+                    const float4 ya = *(const float4 *)(s_A + v * ldA + 4 * bj);
+                    const float xs[4] = {xa.x, xa.y, xa.z, xa.w}, ys[4] = {ya.x, ya.y, ya.z, ya.w};
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                      for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(xs[ii], ys[jj], acc[ii][jj]);
+                  }
+                }
+              }
+              if (blk < nblk)
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                  for (int jj = 0; jj < 4; ++jj) {
+                    const int ra = 4 * bi + ii, rb = 4 * bj + jj;
+                    if (ra < nm && rb < nm && (bi != bj || ii <= jj))
+                      hp[pk(cols[rb], cols[ra])] += acc[ii][jj];  // cols ascending: F position ra <= rb
+                  }
+            }
+            __syncthreads();
+          }
+        }
+        ++nsync;
+        if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
+        if (nf > 0) {  // CTA b sums its share of the entries over the CTAs (compensated, fixed order)
+          const int HPF = nf * (nf + 1) / 2, per = (HPF + G - 1) / G;
+          const int q0 = blockIdx.x * per, q1 = min(HPF, q0 + per);
+          float2 *s_w2 = (float2 *)(s_res + 32);  // [nwarp][32]
+          for (int e0 = q0; e0 < q1; e0 += 32) {
+            const int e = e0 + lane;
+            float cs = 0.f, cc = 0.f;
+            for (int c0 = warp; c0 < G; c0 += 8 * nwarp) {
+              float xv[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int c = c0 + u * nwarp;
+                xv[u] = (c < G && e < q1) ? __ldcg(a.hpart + (size_t)c * HPM + e) : 0.f;
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) comp_add(cs, cc, xv[u]);
+            }
+            s_w2[warp * 32 + lane] = make_float2(cs, cc);
+            __syncthreads();
+            if (warp == 0 && e < q1) {
+              float S = 0.f, C = 0.f;
+              for (int q = 0; q < nwarp; ++q) {
+                const float2 v = s_w2[q * 32 + lane];
+                comp_add(S, C, v.x);
+                C = __fadd_rn(C, v.y);
+              }
+              a.hred[e] = __fadd_rn(S, C);
+            }
+            __syncthreads();
+          }
+        }
+        ++nsync;
+        if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
+        // ---- solve H_F'F' x = -g_F', F' = F without the variables at zero
+        // that the step would push below zero; then the longest step in [0, 1]
+        // that keeps y >= 0 (ratio test; a per-variable projection of a step
+        // scaled by a full inverse Hessian need not descend).  Any failure:
+        // the gradient-projection step.
+        int n = nf;
+        for (int q = tid; q < nf; q += nthr) s_sub[q] = q;
+        __syncthreads();
+        bool solved = false;
+        for (int rep = 0; rep < 8 && n > 0; ++rep) {
+          const int tot = (n + 1) * (n + 2) / 2;
+          for (int q = tid; q < tot; q += nthr) {
+            int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+            while (pk(i, 0) > q) --i;
+            while (pk(i + 1, 0) <= q) ++i;
+            const int j = q - pk(i, 0);
+            float v;
+            if (i == n) {
+              v = j == n ? 0.f : -(float)s_g[s_fidx[s_sub[j]]];
+            } else {
+              const int fi = s_sub[i], fj = s_sub[j];
+              const int ki = s_beam[s_fidx[fi]], kj = s_beam[s_fidx[fj]];
+              double lap = 0.0;  // Laplacian of G (Eq. 2) at (ki, kj)
+              if (ki == kj) {
+                lap = s_igl[ki] + s_igr[ki];
+              } else {
+                if (kj == (ki + 1) % N) lap -= s_igr[ki];
+                if (ki == (kj + 1) % N) lap -= s_igr[kj];
+              }
+              v = __ldcg(a.hred + pk(fi, fj)) + (float)(2.0 * a.gamma * lap);
+              if (i == j) v *= 1.f + 1e-6f;
+            }
+            s_A[q] = v;
+          }
+          __syncthreads();
+          if (!chol_packed_aug(s_A, n, s_cb, s_dg)) break;
+          if (warp == 0) {  // back substitution L^T x = y
+            for (int k = n - 1; k >= 0; --k) {
+              float acc = 0.f;
+              for (int i = k + 1 + lane; i < n; i += 32) acc = fmaf(s_A[pk(i, k)], s_x[i], acc);
+              acc = warp_sumf(acc);
+              if (lane == 0) s_x[k] = (s_A[pk(n, k)] - acc) / s_dg[k];
+              __syncwarp();
+            }
+          }
+          __syncthreads();
+          if (tid == 0) {  // drop variables at zero that the step pushes below zero
+            int nk = 0;
+            for (int i = 0; i < n; ++i) {
+              const int fi = s_sub[i];
+              if (!(s_y[s_beam[s_fidx[fi]]] <= 0.0 && s_x[i] < 0.f)) {
+                s_sub[nk] = fi;
+                s_x[nk] = s_x[i];
+                ++nk;
+              }
+            }
+            s_i[4] = nk;
+          }
+          __syncthreads();
+          const int nk = s_i[4];
+          if (nk == n) { solved = true; break; }
+          n = nk;
+        }
+        if (solved) {
+          // ratio test in FP64: tmax = min(1, min_{x_i < 0} y_i / -x_i), a
+          // minimum of non-negative doubles taken on their bit patterns;
+          // d = tmax x on F', 0 elsewhere, kept only if it descends (g.d < 0)
+          unsigned long long tb = __double_as_longlong(1.0);
+          for (int i = tid; i < n; i += nthr) {
+            const double xi = (double)s_x[i];
+            if (xi < 0.0) {
+              const double r = s_y[s_beam[s_fidx[s_sub[i]]]] / -xi;
+              tb = min(tb, (unsigned long long)__double_as_longlong(r));
+            }
+          }
+          for (int o = 16; o; o >>= 1) tb = min(tb, __shfl_xor_sync(FULL, tb, o));
+          unsigned long long *s_tb = (unsigned long long *)(s_res + 32);  // [nwarp]
+          if (lane == 0) s_tb[warp] = tb;
+          for (int s = tid; s < ns; s += nthr) s_d[s_beam[s]] = 0.0;
+          __syncthreads();
+          tb = s_tb[0];
+          for (int q = 1; q < nwarp; ++q) tb = min(tb, s_tb[q]);
+          const double tmax = __longlong_as_double((long long)tb);
+          float gd = 0.f;
+          for (int i = tid; i < n; i += nthr) {
+            const int sl = s_fidx[s_sub[i]];
+            const double di = tmax * (double)s_x[i];
+            s_d[s_beam[sl]] = di;
+            gd = fmaf((float)s_g[sl], (float)di, gd);
+          }
+          for (int o = 16; o; o >>= 1) gd += __shfl_xor_sync(FULL, gd, o);
+          float *s_gd = (float *)(s_res + 32 + 16);  // [nwarp]
+          if (lane == 0) s_gd[warp] = gd;
+          __syncthreads();
+          gd = 0.f;
+          for (int q = 0; q < nwarp; ++q) gd += s_gd[q];
+          newton_ok = tmax > 0.0 && gd < 0.f;  // same in every thread
+          __syncthreads();
+        }
+        for (int q = tid; q < rows_len; q += nthr) s_rows[q] = 0.f;  // the line search needs them zero
+      }
       float g0 = 0.f;
       for (int s = tid; s < ns; s += nthr) {
         const int k = s_beam[s];
         const double yk = s_y[k], gk = s_g[s];
-        const double p = yk - step * gk;
-        const double dk = (p > 0.0 ? p : 0.0) - yk;
-        s_d[k] = dk;
+        double dk;
+        if (newton_ok) {
+          dk = s_d[k];
+        } else {
+          const double p = yk - step * gk;
+          dk = (p > 0.0 ? p : 0.0) - yk;
+          s_d[k] = dk;
+        }
         s_df[s] = (float)dk;
         s_gold[s] = gk;
         g0 = fmaf((float)gk, (float)dk, g0);
@@ -677,7 +977,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       const int k = s_beam[s];
       const double dy = t * s_d[k];
       s_dy[s] = dy;
-      s_y[k] += dy;
+      s_y[k] = NEWTON ? fmax(s_y[k] + dy, 0.0) : s_y[k] + dy;  // ratio test in FP64: clamp -0
       s_yf[s] = (float)s_y[k];
     }
     const float tf = (float)t;
@@ -776,19 +1076,37 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 }
 
 // ---------------------------------------------------------------- launch
-static size_t master_smem_bytes(int N, int nthr, int vpt) {
-  const size_t ng = vpt / 4, tile = (size_t)nthr * (vpt + 33);  // F' tile + line-search rows
-  return (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +
-         (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + tile * 4 + (size_t)N * ng * 4 +
-         (size_t)(8 + 4 * N + 1 + N * ng) * 4 + 16;
+static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
+  const size_t ng = vpt / 4;
+  size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
+             (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + // yf df tab t ls
+             16 +                                              // alignment of the F' tile
+             (size_t)nthr * vpt * 4 +                          // F' tile
+             (size_t)master_rows_len(N, nthr, newton) * 4 +    // line-search rows (+ Newton staging)
+             (size_t)N * ng * 4 +                              // pair partials
+             (size_t)(8 + 4 * N + 1 + N * ng) * 4;             // i beam nz mask pst pair
+  if (newton) b += (size_t)(2 * N + 8 + ng * N) * 4 + (size_t)(2 * N + 2 * (N + 1)) * 4;
+  return b + 16;
 }
 
-template <int VPT>
+template <int VPT, bool NEWTON>
 static cudaError_t master_occupancy(int nthr, size_t smem, int *nb) {
-  cudaError_t e = cudaFuncSetAttribute(k_master<VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_master<VPT, NEWTON>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_master<VPT>, nthr, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_master<VPT, NEWTON>, nthr, smem);
+}
+
+static cudaError_t master_occupancy_any(int vpt, bool newton, int nthr, size_t smem, int *nb) {
+  if (newton)
+    return vpt == 4    ? master_occupancy<4, true>(nthr, smem, nb)
+           : vpt == 8  ? master_occupancy<8, true>(nthr, smem, nb)
+           : vpt == 16 ? master_occupancy<16, true>(nthr, smem, nb)
+                       : master_occupancy<32, true>(nthr, smem, nb);
+  return vpt == 4    ? master_occupancy<4, false>(nthr, smem, nb)
+         : vpt == 8  ? master_occupancy<8, false>(nthr, smem, nb)
+         : vpt == 16 ? master_occupancy<16, false>(nthr, smem, nb)
+                     : master_occupancy<32, false>(nthr, smem, nb);
 }
 
 // Launch shape: the fewest voxels per thread (4, 8, 16, 32) that fit the
@@ -812,24 +1130,37 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   if (nthr > 512) nthr = 512;
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
-  size_t smem = master_smem_bytes(ctx->N, nthr, vpt);
+  size_t smem = master_smem_bytes(ctx->N, nthr, vpt, false);
+  size_t smem_pn = master_smem_bytes(ctx->N, nthr, vpt, true);
   int nb = 0;
-  cudaError_t e = vpt == 4    ? master_occupancy<4>(nthr, smem, &nb)
-                  : vpt == 8  ? master_occupancy<8>(nthr, smem, &nb)
-                  : vpt == 16 ? master_occupancy<16>(nthr, smem, &nb)
-                              : master_occupancy<32>(nthr, smem, &nb);
+  cudaError_t e = master_occupancy_any(vpt, false, nthr, smem, &nb);
   if (e != cudaSuccess) return vmat_cuda_fail(ctx, e, "master occupancy");
   if (nb < 1 || grid > nb * ctx->num_sms)
     return vmat_fail(ctx, VMAT_EINVAL, "master kernel cannot be co-resident (%d blocks/SM)", nb);
+  if (ctx->master_method == VMAT_MASTER_PROJECTED_NEWTON) {
+    int optin = 0;
+    VMAT_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (smem_pn > (size_t)optin)
+      return vmat_fail(ctx, VMAT_EINVAL,
+                       "projected-Newton master needs %zu B of shared memory per CTA (%d beams); "
+                       "the device allows %d", smem_pn, ctx->N, optin);
+    e = master_occupancy_any(vpt, true, nthr, smem_pn, &nb);
+    if (e != cudaSuccess) return vmat_cuda_fail(ctx, e, "projected-Newton master occupancy");
+    if (nb < 1 || grid > nb * ctx->num_sms)
+      return vmat_fail(ctx, VMAT_EINVAL, "projected-Newton master cannot be co-resident");
+  }
   ctx->master_vpt = vpt;
   ctx->master_block = nthr;
   ctx->master_grid = grid;
   ctx->master_smem = smem;
+  ctx->master_smem_pn = smem_pn;
   ctx->Vpad = (int32_t)(grid * chunk);
   return VMAT_OK;
 }
 
 int64_t vmat_master_scratch(int grid, int N) { return (int64_t)grid * (N + PART_EXTRA) + N; }
+
+int64_t vmat_hessian_len(int N) { return (int64_t)(N + 1) * (N + 2) / 2; }
 
 vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, double rho_ref,
                                int set_rho_plan, double *rec_cost, double *rec_rho,
@@ -861,6 +1192,10 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   a.fp_out = ctx->fpact;
   a.out = ctx->mout;
   a.stats = ctx->mstats;
+  const bool pn = ctx->master_method == VMAT_MASTER_PROJECTED_NEWTON;
+  if (pn && !ctx->hbuf) return vmat_fail(ctx, VMAT_ESTATE, "projected-Newton scratch missing");
+  a.hpart = pn ? ctx->hbuf : nullptr;
+  a.hred = pn ? ctx->hbuf + (size_t)ctx->master_grid * vmat_hessian_len(ctx->N) : nullptr;
   a.rec_cost = rec_cost;
   a.rec_rho = rec_rho;
   a.rec_iters = rec_iters;
@@ -872,18 +1207,23 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, ctx->stream));
   void *args[] = {&a};
   dim3 grid(ctx->master_grid), block(ctx->master_block);
-  const void *fn = ctx->master_vpt == 4    ? (const void *)k_master<4>
-                   : ctx->master_vpt == 8  ? (const void *)k_master<8>
-                   : ctx->master_vpt == 16 ? (const void *)k_master<16>
-                                           : (const void *)k_master<32>;
+  const int v = ctx->master_vpt;
+  const void *fn = pn ? (v == 4    ? (const void *)k_master<4, true>
+                         : v == 8  ? (const void *)k_master<8, true>
+                         : v == 16 ? (const void *)k_master<16, true>
+                                   : (const void *)k_master<32, true>)
+                      : (v == 4    ? (const void *)k_master<4, false>
+                         : v == 8  ? (const void *)k_master<8, false>
+                         : v == 16 ? (const void *)k_master<16, false>
+                                   : (const void *)k_master<32, false>);
+  const size_t smem = pn ? ctx->master_smem_pn : ctx->master_smem;
   // the dynamic shared-memory limit is a per-kernel, process-wide attribute:
   // set it for this context's launch (another context may have lowered it)
-  VMAT_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)ctx->master_smem));
+  VMAT_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t lc = {};
   lc.gridDim = grid;
   lc.blockDim = block;
-  lc.dynamicSmemBytes = ctx->master_smem;
+  lc.dynamicSmemBytes = smem;
   lc.stream = ctx->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident (the grid waits on itself)

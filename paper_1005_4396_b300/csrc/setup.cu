@@ -287,6 +287,10 @@ static vmat_status alloc_tiled(vmat_ctx *ctx) {
   if (nbv * 32 > need) need = nbv * 32;
   ctx->red_len = need + 128;
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->red, ctx->red_len));
+  if (ctx->master_method == VMAT_MASTER_PROJECTED_NEWTON) {
+    ctx->hbuf_len = (int64_t)(ctx->master_grid + 1) * vmat_hessian_len(N);
+    VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->hbuf, ctx->hbuf_len));
+  }
   return VMAT_OK;
 }
 
@@ -303,6 +307,12 @@ static void free_tiled(vmat_ctx *ctx) {
       *ptrs[q] = nullptr;
       ctx->device_bytes -= (int64_t)bytes[q];
     }
+  if (ctx->hbuf) {
+    cudaFree(ctx->hbuf);
+    ctx->hbuf = nullptr;
+    ctx->device_bytes -= ctx->hbuf_len * 4;
+    ctx->hbuf_len = 0;
+  }
 }
 
 extern "C" vmat_status vmat_set_master_budget(vmat_ctx *ctx, int32_t max_ctas) {
@@ -322,6 +332,26 @@ extern "C" vmat_status vmat_set_master_budget(vmat_ctx *ctx, int32_t max_ctas) {
   s = alloc_tiled(ctx);
   if (s != VMAT_OK) return s;
   return vmat_reset(ctx);
+}
+
+extern "C" vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method) {
+  if (!ctx) return VMAT_EINVAL;
+  if (method != VMAT_MASTER_PROJECTED_GRADIENT && method != VMAT_MASTER_PROJECTED_NEWTON)
+    return vmat_fail(ctx, VMAT_EINVAL, "unknown master method %d", method);
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int old = ctx->master_method;
+  ctx->master_method = method;
+  vmat_status s = vmat_configure_master(ctx);  // same tiling; checks the variant fits an SM
+  if (s != VMAT_OK) {
+    ctx->master_method = old;
+    vmat_configure_master(ctx);
+    return s;
+  }
+  if (method == VMAT_MASTER_PROJECTED_NEWTON && !ctx->hbuf) {
+    ctx->hbuf_len = (int64_t)(ctx->master_grid + 1) * vmat_hessian_len(ctx->N);
+    VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->hbuf, ctx->hbuf_len));
+  }
+  return VMAT_OK;
 }
 
 static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_t st,

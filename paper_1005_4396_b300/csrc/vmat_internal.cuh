@@ -95,6 +95,10 @@ struct vmat_ctx {
   int64_t n_launches = 0;      // kernels launched by this context
   int profiling = 0;
   int sm_budget = 0;           // master kernel CTA budget (0: every SM)
+  int master_method = 0;       // VMAT_MASTER_PROJECTED_GRADIENT or _NEWTON
+  size_t master_smem_pn = 0;   // shared memory of the projected-Newton variant
+  float *hbuf = nullptr;       // projected Newton: [grid + 1][(N+1)(N+2)/2] Gram partials + sum
+  int64_t hbuf_len = 0;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -154,6 +158,7 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
 vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const float *colw, float *G);
 vmat_status vmat_configure_master(vmat_ctx *ctx);
 int64_t vmat_master_scratch(int grid, int N);
+int64_t vmat_hessian_len(int N);
 vmat_status vmat_enqueue_reset(vmat_ctx *ctx);
 
 // Device-resident per-iteration records of a column-generation run.

@@ -97,6 +97,7 @@ EXPORTS = {
     "vmat_batch_tune": [_p, _i32, _i32, _d, _p, _p],
     "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
+    "vmat_set_master_method": [_p, _i32],
 }
 
 _lib = None
@@ -382,6 +383,10 @@ class Plan:
     def reset(self):
         vmat_reset(self.ctx)
 
+    def set_master_method(self, method):
+        """'pg' (the paper's gradient projection, default) or 'newton'."""
+        vmat_set_master_method(self.ctx, method)
+
     def set_profiling(self, on=True):
         vmat_set_profiling(self.ctx, on)
 
@@ -409,6 +414,15 @@ class Plan:
         G = self._t(self.cfg.n_beamlets * 32)
         vmat_price_batch32(self.ctx, Fp, G, w)
         return G
+
+
+VMAT_MASTER_PROJECTED_GRADIENT = 0
+VMAT_MASTER_PROJECTED_NEWTON = 1
+MASTER_METHODS = {"pg": VMAT_MASTER_PROJECTED_GRADIENT, "newton": VMAT_MASTER_PROJECTED_NEWTON}
+
+
+def vmat_set_master_method(ctx, method):
+    _check(ctx, load_library().vmat_set_master_method(ctx, int(MASTER_METHODS.get(method, method))))
 
 
 def vmat_set_master_budget(ctx, max_ctas):

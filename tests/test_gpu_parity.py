@@ -241,6 +241,26 @@ def test_colgen_small_path_neighbours(small):
     np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
 
 
+@pytest.mark.parametrize("method", ["pg", "newton"])
+def test_colgen_odd_beam_count(small, method):
+    """An odd number of beams (13) changes the shared-memory carve-up of the
+    master kernel; both master methods still match the oracle."""
+    cfg = inputs.small_config(n_angles=13)
+    prob = inputs.make_problem(cfg)
+    ref = oracle.colgen(prob, eps=1e-8)
+    with vmat.Plan(prob) as plan:
+        plan.set_master_method(method)
+        gpu = plan.colgen_run(kkt_tol=1e-6)
+        first = _compare_decisions(gpu, ref, cfg.n_rows)
+        np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
+        R = cfg.n_rows
+        fl = np.array([ref["lleaf"][k * R:(k + 1) * R] for k in ref["k"]])
+        fr = np.array([ref["rleaf"][k * R:(k + 1) * R] for k in ref["k"]])
+        plan.reset()
+        rep = plan.colgen_run(kkt_tol=1e-6, forced=(ref["k"], fl, fr))
+        np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
+
+
 # ------------------------------------------------------------------ batched (differentiable) forms
 def test_batch32_parity(small, small_plan):
     prob = small
