@@ -293,9 +293,9 @@ def run_ours(args):
            "clocks": clocks}
 
     if rank == 0 and ws == 1 and not args.quick:
+        out["variants"] = run_variants(prob, plan, recs[-1], kkt)  # reads this plan's state first
         if args.master == "pg":
             out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
-        out["variants"] = run_variants(prob, plan, recs[-1], kkt)
         out["e2e"] = run_e2e(prob, args)
         out["cpu_baseline"] = run_cpu_baseline(prob, args)
     plan.close()
