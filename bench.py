@@ -110,6 +110,19 @@ def _dist():
     return ws, rank, local
 
 
+def _aggregate(ms_local, ws, steps, units_per_step, device):
+    """Whole-job throughput of `ws` replicas (one per GPU, independent plans,
+    no data-path collective): the slowest rank's time (all-reduce MAX over
+    the timed region) and every rank's units over it."""
+    ms = float(ms_local)
+    if ws > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * steps * units_per_step / (ms / 1e3)
+
+
 def _workload(name):
     from paper_1005_4396_b300 import inputs
     return {"prostate": inputs.prostate_config, "tiny": inputs.tiny_config,
@@ -202,14 +215,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = plan.launches() - l0
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    iters_per_plan = cfg.iterations
-    total_units = ws * args.steps * iters_per_plan
-    value = total_units / (ms / 1e3)
+    ms, value = _aggregate(ev0.elapsed_time(ev1), ws, args.steps, cfg.iterations, "cuda")
 
     # per-phase device time and the roofline of the dominant kernel
     phase = np.sum([r["phase_ms"] for r in recs], axis=0)  # [n_iter, 4]
