@@ -601,7 +601,7 @@ def run_autograd(args):
 def run_case(args):
     """Small cases sized for an ncu capture (a few GB on the device, inputs
     larger than L2): the prostate phantom cut to 32 slices (V_active 221k,
-    nnz 2.2e8).  master: 150 seeded apertures, one master launch of 30
+    nnz 2.2e8).  master: --case-cols seeded apertures (150), one master launch of 30
     projected-gradient iterations.  spmv: dose and price SpMV, twice each."""
     import torch
     from paper_1005_4396_b300 import inputs, vmat
@@ -613,12 +613,12 @@ def run_case(args):
     if args.case == "master":
         R = cfg.n_rows
         ll, rr = inputs.random_apertures(7, cfg)
-        beams = np.random.default_rng(7).permutation(cfg.n_angles)[:150]
+        beams = np.random.default_rng(7).permutation(cfg.n_angles)[:args.case_cols]
         for k in beams:
             plan.add_column(int(k), ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
         y = np.zeros(cfg.n_angles)
         res = plan.master_step(max_iters=30, kkt_tol=1e-9, y=y)
-        out.update(columns=150, master=res)
+        out.update(columns=int(args.case_cols), master=res)
     else:
         x = torch.rand(prob.n_beamlets, device="cuda")
         f = torch.randn(prob.n_vox, device="cuda")
@@ -674,6 +674,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--case", default=None, choices=["master", "spmv"],
                     help="small case for an ncu capture instead of the benchmark")
+    ap.add_argument("--case-cols", type=int, default=150,
+                    help="columns of the --case master launch (150: ~133 MB, above L2)")
     ap.add_argument("--batched", action="store_true",
                     help="the sixteen-plan batch (FP16-D, graph) against the FP32 single-plan loop")
     ap.add_argument("--batch-scale", type=float, default=1.0)

@@ -348,13 +348,15 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   int *s_slot = (int *)(s_igr + N);  // [N] slot of each beam, -1 if none (N doubles reserved)
   double *s_sc = s_igr + 2 * N;      // [32] CTA-wide scalars
   double *s_res = s_sc + 32;         // [32 + 16*32] line-search sums and scratch
-  float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [N] per slot
-  float *s_df = s_yf + N;                         // [N] per slot
-  float *s_tab = s_df + N;                        // [768]
+  const int Np = (N + 1) & ~1;                    // keeps the float region below 16-byte aligned
+  float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [Np] per slot
+  float *s_df = s_yf + Np;                        // [Np] per slot
+  float *s_tab = s_df + Np;                       // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
   float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
-  // 16-byte aligned for float4 access (the sizes above leave 8-byte alignment when N is odd)
-  float *s_fp = (float *)(((uintptr_t)(s_ls + 16 * 32) + 15) & ~(uintptr_t)15);  // [NG][ST] F' (pass A)
+  // s_fp is 16-byte aligned for its float4 accesses: the doubles above take a
+  // multiple of 16 bytes and the floats (2 Np + 1296) a multiple of 4
+  float *s_fp = s_ls + 16 * 32;  // [NG][ST] F' (pass A)
   float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
   const int rows_len = master_rows_len(N, nthr, NEWTON);
   float *s_pp = s_rows + rows_len;                // [N*NG] warp partial per (slot, subtile) pair
@@ -1079,8 +1081,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
   const size_t ng = vpt / 4;
   size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
-             (size_t)(2 * N + 768 + LS_POINTS + 16 * 32) * 4 + // yf df tab t ls
-             16 +                                              // alignment of the F' tile
+             (size_t)(2 * ((N + 1) & ~1) + 768 + LS_POINTS + 16 * 32) * 4 +  // yf df tab t ls
              (size_t)nthr * vpt * 4 +                          // F' tile
              (size_t)master_rows_len(N, nthr, newton) * 4 +    // line-search rows (+ Newton staging)
              (size_t)N * ng * 4 +                              // pair partials
@@ -1111,7 +1112,8 @@ static cudaError_t master_occupancy_any(int vpt, bool newton, int nthr, size_t s
 
 // Launch shape: the fewest voxels per thread (4, 8, 16, 32) that fit the
 // SMs with 512-thread CTAs, then threads per CTA chosen so that about
-// MASTER_CTA_TARGET CTAs cover the voxels.  Fewer, larger CTAs make the grid
+// MASTER_CTA_TARGET CTAs cover the voxels (512 threads from 16 voxels per
+// thread on: there the extra warps hide more latency than fewer CTAs save).  Fewer, larger CTAs make the grid
 // barriers and cross-CTA sums of every iteration cheaper; on B300 ~110 CTAs
 // still stream the columns at full bandwidth, while more voxels per thread
 // (16, 32) lengthen every per-voxel pass.
@@ -1127,7 +1129,7 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   const int64_t per = (Va + (int64_t)vpt * target - 1) / ((int64_t)vpt * target);
   int nthr = (int)(((per + 31) / 32) * 32);
   if (nthr < 64) nthr = 64;
-  if (nthr > 512) nthr = 512;
+  if (nthr > 512 || vpt >= 16) nthr = 512;  // at 16+ voxels per thread every warp counts
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
   size_t smem = master_smem_bytes(ctx->N, nthr, vpt, false);
