@@ -273,12 +273,26 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
   return true;
 }
 
+// Asynchronous 16-byte global -> shared copies (bypassing L1): a thread keeps
+// several column segments in flight without holding them in registers.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stages of the direction pass's copy pipeline: column segments in flight per thread
+__host__ __device__ constexpr int master_pipe_stages(int vpt) { return vpt >= 16 ? 8 : 16; }
+
 // Floats of the region holding the line-search rows ([nthr][33]); the
-// projected-Newton variant also stages its Gram chunks ([64][N+8]) and its
+// direction pass runs its copy pipeline ([stages][nthr] float4) there, and
+// the projected-Newton variant stages its Gram chunks ([64][N+8]) and its
 // packed factor ((N+1)(N+2)/2) there.  A multiple of 4 (keeps what follows
 // 16-byte aligned).
-__host__ __device__ __forceinline__ int master_rows_len(int N, int nthr, bool newton) {
-  int r = 33 * nthr;
+__host__ __device__ __forceinline__ int master_rows_len(int N, int nthr, int vpt, bool newton) {
+  int r = max(33, 4 * master_pipe_stages(vpt)) * nthr;  // rows; direction-pass pipeline
   if (newton) {
     const int st = 64 * (N + 8), fac = (N + 1) * (N + 2) / 2;
     r = max(r, max(st, fac));
@@ -358,7 +372,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   // multiple of 16 bytes and the floats (2 Np + 1296) a multiple of 4
   float *s_fp = s_ls + 16 * 32;  // [NG][ST] F' (pass A)
   float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
-  const int rows_len = master_rows_len(N, nthr, NEWTON);
+  const int rows_len = master_rows_len(N, nthr, VPT, NEWTON);
   float *s_pp = s_rows + rows_len;                // [N*NG] warp partial per (slot, subtile) pair
   int *s_i = (int *)(s_pp + N * NG);              // [8]: 1 nonzero slots, 2 nonzero pairs
   int *s_beam = s_i + 8;                          // [N] beam of slot
@@ -366,8 +380,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   int *s_mask = s_nz + N;                         // [N] per slot: bit m = subtile m nonzero
   int *s_pst = s_mask + N;                        // [N+1] first pair of each slot
   int *s_pair = s_pst + N + 1;                    // [N*NG] pairs s*8+m in slot order
+  int *s_mcnt = s_pair + N * NG;                  // [8] nonzero columns of each own subtile
+  int *s_mcols = s_mcnt + 8;                      // [NG][N] those columns (slots), ascending
   // projected Newton only (the launch sizes these for that variant)
-  int *s_fidx = s_pair + N * NG;                  // [N] free slots F, in slot order
+  int *s_fidx = s_mcols + N * NG;                 // [N] free slots F, in slot order
   int *s_sub = s_fidx + N;                        // [N] F positions kept after dropping blocked ones
   int *s_ncol = s_sub + N;                        // [8] free columns nonzero in each own subtile
   int *s_cols = s_ncol + 8;                       // [NG][N] their F positions
@@ -418,6 +434,12 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     s_pst[ns] = np;
     s_i[1] = n;
     s_i[2] = np;
+    for (int m = 0; m < NG; ++m) {
+      int c = 0;
+      for (int s = 0; s < ns; ++s)
+        if (s_mask[s] >> m & 1) s_mcols[m * N + c++] = s;
+      s_mcnt[m] = c;
+    }
   }
   __syncthreads();
   for (int s = tid; s < ns; s += nthr) s_yf[s] = (float)s_y[s_beam[s]];
@@ -843,22 +865,43 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[1] += c1 - s_clk[4]; s_clk[4] = c1; }
 
     // ---------------- pass B: z = M y, w = M d
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) { z[v] = 0.f; w[v] = 0.f; }
-#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
-    for (int q = 0; q < nnzs; ++q) {
-      const int s = s_nz[q], mk = s_mask[s];
-      const float *Ms = a.M + (size_t)s * a.Vpad;
-      const float ys = s_yf[s], ds = s_df[s];
+    // per own subtile, the thread streams its 16 bytes of each nonzero column
+    // through a private ring of shared-memory slots (STG copies in flight;
+    // the columns are mostly L2-resident, so latency bounds this pass)
+    {
+      constexpr int STG = master_pipe_stages(VPT);
+      float4 *pipe = (float4 *)s_rows;  // [STG][nthr], slot k of thread t at k*nthr + t
 #pragma unroll
       for (int m = 0; m < NG; ++m) {
-        if (!(mk >> m & 1)) continue;
-        const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
-        z[4 * m] = fmaf(q.x, ys, z[4 * m]);         w[4 * m] = fmaf(q.x, ds, w[4 * m]);
-        z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]); w[4 * m + 1] = fmaf(q.y, ds, w[4 * m + 1]);
-        z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]); w[4 * m + 2] = fmaf(q.z, ds, w[4 * m + 2]);
-        z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]); w[4 * m + 3] = fmaf(q.w, ds, w[4 * m + 3]);
+        const int nm = s_mcnt[m];
+        const int *cl = s_mcols + m * N;
+        const float *src = a.M + SUB_OFF(m) + 4 * tid;
+        float4 zz = make_float4(0.f, 0.f, 0.f, 0.f), ww = zz;
+#pragma unroll
+        for (int k = 0; k < STG; ++k) {
+          if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
+          cp_async_commit();
+        }
+        for (int q = 0; q < nm; ++q) {
+          cp_async_wait<STG - 1>();
+          const int slot = q & (STG - 1);
+          const float4 v = pipe[slot * nthr + tid];
+          const int sl = cl[q];
+          const float ys = s_yf[sl], ds = s_df[sl];
+          zz.x = fmaf(v.x, ys, zz.x); ww.x = fmaf(v.x, ds, ww.x);
+          zz.y = fmaf(v.y, ys, zz.y); ww.y = fmaf(v.y, ds, ww.y);
+          zz.z = fmaf(v.z, ys, zz.z); ww.z = fmaf(v.z, ds, ww.z);
+          zz.w = fmaf(v.w, ys, zz.w); ww.w = fmaf(v.w, ds, ww.w);
+          if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
+          cp_async_commit();
+        }
+        z[4 * m] = zz.x; z[4 * m + 1] = zz.y; z[4 * m + 2] = zz.z; z[4 * m + 3] = zz.w;
+        w[4 * m] = ww.x; w[4 * m + 1] = ww.y; w[4 * m + 2] = ww.z; w[4 * m + 3] = ww.w;
       }
+      cp_async_wait<0>();
+      __syncthreads();  // every thread's copies have landed before the rows are reused
+#pragma unroll
+      for (int p = 0; p < 33; ++p) s_rows[tid * 33 + p] = 0.f;
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[2] += c1 - s_clk[4]; s_clk[4] = c1; }
 
@@ -1083,9 +1126,10 @@ static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
   size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
              (size_t)(2 * ((N + 1) & ~1) + 768 + LS_POINTS + 16 * 32) * 4 +  // yf df tab t ls
              (size_t)nthr * vpt * 4 +                          // F' tile
-             (size_t)master_rows_len(N, nthr, newton) * 4 +    // line-search rows (+ Newton staging)
+             (size_t)master_rows_len(N, nthr, vpt, newton) * 4 +  // line-search rows, pipeline, Newton
              (size_t)N * ng * 4 +                              // pair partials
-             (size_t)(8 + 4 * N + 1 + N * ng) * 4;             // i beam nz mask pst pair
+             (size_t)(8 + 4 * N + 1 + N * ng) * 4 +            // i beam nz mask pst pair
+             (size_t)(8 + N * ng) * 4;                          // per-subtile column lists
   if (newton) b += (size_t)(2 * N + 8 + ng * N) * 4 + (size_t)(2 * N + 2 * (N + 1)) * 4;
   return b + 16;
 }
