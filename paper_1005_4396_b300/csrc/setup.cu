@@ -517,7 +517,8 @@ extern "C" void vmat_destroy(vmat_ctx *ctx) {
                   ctx->vm_col, ctx->vm_val, ctx->M, ctx->tflag, ctx->occ, ctx->lleaf, ctx->rleaf,
                   ctx->slot_beam, ctx->y, ctx->zact, ctx->fpact, ctx->rho_plan, ctx->g,
                   ctx->fgather, ctx->xs, ctx->ap_price, ctx->ap_l, ctx->ap_r, ctx->sel, ctx->sel_l,
-                  ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats};
+                  ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats,
+                  ctx->hbuf};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;

@@ -32,7 +32,7 @@ def _rank(rank, ws, port, times, out):
 
 def test_two_replicas_take_the_slowest_rank():
     ws, times = 2, [1500.0, 1900.0]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.start_processes(_rank, args=(ws, _free_port(), times, out), nprocs=ws, start_method="spawn")
     assert out[0] == out[1]
     ms, value = out[0]
