@@ -294,7 +294,7 @@ __host__ __device__ constexpr int master_pipe_stages(int vpt) { return vpt >= 16
 __host__ __device__ __forceinline__ int master_rows_len(int N, int nthr, int vpt, bool newton) {
   int r = max(33, 4 * master_pipe_stages(vpt)) * nthr;  // rows; direction-pass pipeline
   if (newton) {
-    const int st = 64 * (N + 8), fac = (N + 1) * (N + 2) / 2;
+    const int st = 64 * (N + 8) + 16 * nthr, fac = (N + 1) * (N + 2) / 2;  // staging + slice partials
     r = max(r, max(st, fac));
   }
   return (r + 3) & ~3;
@@ -633,15 +633,22 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         if (nf > 0) {
           float *hp = a.hpart + (size_t)blockIdx.x * HPM;
           for (int q = tid; q < nf * (nf + 1) / 2; q += nthr) hp[q] = 0.f;
+          float *s_part = s_A + 64 * (N + 8);  // [nthr][16] partial blocks of the voxel slices
           for (int m = 0; m < NG; ++m) {
             const int nm = s_ncol[m];
             if (nm == 0) continue;
             const int P = (nm + 3) >> 2, ldA = 4 * P + 4, nblk = P * (P + 1) / 2;
             const int *cols = s_cols + m * N;
-            for (int blk0 = 0; blk0 < nblk; blk0 += nthr) {
-              const int blk = blk0 + tid;
+            // KS voxel slices per 4x4 block when there are fewer blocks than
+            // threads; the slices' partial blocks are added in slice order
+            int KS = 1;
+            while (KS < 8 && nblk * KS * 2 <= nthr) KS *= 2;
+            const int bpr = nthr / KS, ks = tid / bpr, bl = tid - ks * bpr;
+            for (int blk0 = 0; blk0 < nblk; blk0 += bpr) {
+              const int blk = blk0 + bl;
+              const bool act = ks < KS && blk < nblk;
               int bi = 0, bj = 0;
-              if (blk < nblk) {  // block (bi <= bj) of the upper triangle, row-major
+              if (act) {  // block (bi <= bj) of the upper triangle, row-major
                 int r = 0, rem = blk;
                 while (rem >= P - r) { rem -= P - r; ++r; }
                 bi = r;
@@ -663,9 +670,9 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
                   s_A[v * ldA + row] = val;
                 }
                 __syncthreads();
-                if (blk < nblk) {
+                if (act) {
 #pragma unroll 4
-                  for (int v = 0; v < 64; ++v) {
+                  for (int v = ks; v < 64; v += KS) {
                     const float4 xa = *(const float4 *)(s_A + v * ldA + 4 * bi);
                     const float4 ya = *(const float4 *)(s_A + v * ldA + 4 * bj);
                     const float xs[4] = {xa.x, xa.y, xa.z, xa.w}, ys[4] = {ya.x, ya.y, ya.z, ya.w};
@@ -676,7 +683,17 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
                   }
                 }
               }
-              if (blk < nblk)
+              if (KS > 1) {
+                if (act)
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) s_part[tid * 16 + e] = acc[e >> 2][e & 3];
+                __syncthreads();
+                if (act && ks == 0)
+                  for (int q = 1; q < KS; ++q)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[e >> 2][e & 3] += s_part[(q * bpr + bl) * 16 + e];
+              }
+              if (act && ks == 0)
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
