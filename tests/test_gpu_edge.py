@@ -16,6 +16,12 @@ if not torch.cuda.is_available():
 
 from paper_1005_4396_b300 import vmat  # noqa: E402
 
+# Decisions are compared where both sides priced the same way: the GPU's masters
+# stop at relative KKT 1e-6 (its FP32 floor), the oracle's at 1e-8, so their
+# aperture prices differ by ~1e-6 relative and a decision whose margin lies
+# within 10x of that is a near-tie (pricing on identical prices is bit-exact).
+NEAR_TIE = 1e-5
+
 CASES = {
     "one_beam": dict(n_angles=1),
     "two_beams": dict(n_angles=2),
@@ -44,7 +50,7 @@ def _check_plan(prob, gpu, ref):
         if not (gpu["k"][t] == k and
                 np.array_equal(gpu["lleaf"][k * R:(k + 1) * R], ref["lleaf"][k * R:(k + 1) * R]) and
                 np.array_equal(gpu["rleaf"][k * R:(k + 1) * R], ref["rleaf"][k * R:(k + 1) * R])):
-            assert min(ref["margin"][t], ref["row_margin"][t]) <= 1e-6, f"iteration {t}"
+            assert min(ref["margin"][t], ref["row_margin"][t]) <= NEAR_TIE, f"iteration {t}"
             first = t
             break
     np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)

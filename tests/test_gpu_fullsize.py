@@ -26,6 +26,12 @@ if not torch.cuda.is_available():
 
 from paper_1005_4396_b300 import vmat  # noqa: E402
 
+# Decisions are compared where both sides priced the same way: the GPU's masters
+# stop at relative KKT 1e-6 (its FP32 floor), the oracle's at 1e-8, so their
+# aperture prices differ by ~1e-6 relative and a decision whose margin lies
+# within 10x of that is a near-tie (pricing on identical prices is bit-exact).
+NEAR_TIE = 1e-5
+
 
 @pytest.fixture(scope="module")
 def prostate():
@@ -124,7 +130,7 @@ def test_prostate_pricing_bit_exact_and_columns(prostate, pplan):
     pplan.reset()
 
 
-def _first_difference(gpu, ref, R, tol=1e-6):
+def _first_difference(gpu, ref, R, tol=NEAR_TIE):
     for t in range(len(ref["k"])):
         k = ref["k"][t]
         same = gpu["k"][t] == k and np.array_equal(_leaves(gpu["lleaf"], k, R), _leaves(ref["lleaf"], k, R)) \

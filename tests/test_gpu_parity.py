@@ -16,6 +16,12 @@ if not torch.cuda.is_available():
 
 from paper_1005_4396_b300 import vmat  # noqa: E402
 
+# Decisions are compared where both sides priced the same way: the GPU's masters
+# stop at relative KKT 1e-6 (its FP32 floor), the oracle's at 1e-8, so their
+# aperture prices differ by ~1e-6 relative and a decision whose margin lies
+# within 10x of that is a near-tie (pricing on identical prices is bit-exact).
+NEAR_TIE = 1e-5
+
 
 @pytest.fixture(scope="module")
 def tiny():
@@ -186,7 +192,7 @@ def test_master_parity(tiny, tiny_plan):
 
 
 # ------------------------------------------------------------------ column generation
-def _compare_decisions(gpu, ref, R, tol=1e-6):
+def _compare_decisions(gpu, ref, R, tol=NEAR_TIE):
     """Index of the first iteration whose beam or leaves differ, checking that
     every difference sits on a near-tie (margin <= tol relative)."""
     n = len(ref["k"])
