@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
-# current kernel (bench.py --case master: 8.224058 GB read + 7.762 MB written
+# current kernel (bench.py --case master: 8.215405 GB read + 7.696 MB written
 # for (2*30+2) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
 # to None whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (8.224058e9 + 7.762176e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
+MASTER_TRAFFIC_RATIO = (8.215405e9 + 7.696384e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 
