@@ -52,7 +52,7 @@ struct MasterArgs {
   double *y;             // [N] in/out
   double *rho_plan;      // [1] read (max with rho_ref) and, if set_rho_plan, written
   double *part;          // [grid][N + PART_EXTRA]
-  double *gred;          // [N]
+  float *gpart;          // [grid][(N+3)&~3] per-CTA gradient partials (16-byte aligned rows)
   unsigned *bar;         // [1] grid barrier word
   int *dstatus;
   float *z_out, *fp_out;  // [Vpad]
@@ -515,22 +515,56 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       if (lane == 0) s_pp[q] = acc;
     }
     __syncthreads();
-    for (int s = tid; s < ns; s += nthr) {  // all-zero subtiles contribute exact zeros
-      double acc = 0.0;
-      for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) acc += (double)s_pp[q];
-      a.part[(size_t)blockIdx.x * stride + s] = acc;
+    const int fstride = (N + 3) & ~3;
+    float *grow = a.gpart + (size_t)blockIdx.x * fstride;
+    for (int s = tid; s < ((ns + 3) & ~3); s += nthr) {  // all-zero subtiles contribute exact zeros
+      float cs = 0.f, cc = 0.f;
+      if (s < ns)
+        for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) comp_add(cs, cc, s_pp[q]);
+      grow[s] = __fadd_rn(cs, cc);
     }
     ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
-    // fixed-order sums over CTAs: warp w of CTA b owns slot b + G*w
-    for (int s = blockIdx.x + (int)gridDim.x * warp; s < ns; s += (int)gridDim.x * nwarp) {
-      double acc = 0.0;
-      for (int c = lane; c < (int)gridDim.x; c += 32) acc += __ldcg(a.part + (size_t)c * stride + s);
-      acc = warp_sum(acc);
-      if (lane == 0) a.gred[s] = acc;
+    {  // every CTA sums every CTA's row in the same fixed order (compensated):
+       // warp w takes CTAs w, w + W, ... (8 loads in flight per lane), lane l
+       // slots 4l..4l+3 of each 128-slot chunk; then the warps are combined
+      const int n4 = (ns + 3) >> 2;
+      float2 *s_gw = (float2 *)s_rows;  // [nwarp][128] (the rows are free until pass B)
+      for (int c4 = 0; c4 < n4; c4 += 32) {
+        const int j = c4 + lane;
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+        constexpr int GB = VPT >= 16 ? 4 : 8;  // loads in flight per lane (registers are tight at 16+)
+        for (int c0 = warp; c0 < G; c0 += GB * nwarp) {
+          float4 xv[GB];
+#pragma unroll
+          for (int u = 0; u < GB; ++u) {
+            const int c = c0 + u * nwarp;
+            xv[u] = (c < G && j < n4) ? __ldcg((const float4 *)(a.gpart + (size_t)c * fstride) + j)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < GB; ++u) {
+            comp_add(S[0], C[0], xv[u].x);
+            comp_add(S[1], C[1], xv[u].y);
+            comp_add(S[2], C[2], xv[u].z);
+            comp_add(S[3], C[3], xv[u].w);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s_gw[warp * 128 + 4 * lane + e] = make_float2(S[e], C[e]);
+        __syncthreads();
+        for (int t = tid; t < 128 && 4 * c4 + t < ns; t += nthr) {
+          float gs = 0.f, gc = 0.f;
+          for (int q = 0; q < nwarp; ++q) {
+            const float2 v = s_gw[q * 128 + t];
+            comp_add(gs, gc, v.x);
+            gc = __fadd_rn(gc, v.y);
+          }
+          s_g[4 * c4 + t] = (double)gs + (double)gc;  // M^T F'(z) of slot 4 c4 + t
+        }
+        __syncthreads();
+      }
     }
-    ++nsync;
-    if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[0] += c1 - s_clk[4]; s_clk[4] = c1; }
 
     // ---------------- gradient, residual, direction (same in every CTA)
@@ -547,7 +581,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       float dyg = 0.f, dgg = 0.f;
       for (int s = tid; s < ns; s += nthr) {
         const int k = s_beam[s];
-        const double gk = __ldcg(a.gred + s) + a.gamma * dG_inv(s_y, s_igl, s_igr, N, k);
+        const double gk = s_g[s] + a.gamma * dG_inv(s_y, s_igl, s_igr, N, k);
         s_g[s] = gk;
         const unsigned long long ybits = (unsigned long long)__double_as_longlong(s_y[k]) & ABS;
         const unsigned long long gbits = (unsigned long long)__double_as_longlong(gk);
@@ -1221,7 +1255,11 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   return VMAT_OK;
 }
 
-int64_t vmat_master_scratch(int grid, int N) { return (int64_t)grid * (N + PART_EXTRA) + N; }
+// doubles: per-CTA partial rows [grid][N + PART_EXTRA], then (16-byte
+// aligned) the per-CTA gradient partial rows [grid][(N+3)&~3] floats
+int64_t vmat_master_scratch(int grid, int N) {
+  return (int64_t)grid * (N + PART_EXTRA) + 2 + ((int64_t)grid * ((N + 3) & ~3) + 1) / 2;
+}
 
 int64_t vmat_hessian_len(int N) { return (int64_t)(N + 1) * (N + 2) / 2; }
 
@@ -1248,7 +1286,10 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   a.y = ctx->y;
   a.rho_plan = ctx->rho_plan;
   a.part = ctx->red;
-  a.gred = ctx->red + (size_t)ctx->master_grid * (ctx->N + PART_EXTRA);
+  {
+    const uintptr_t gp = (uintptr_t)(ctx->red + (size_t)ctx->master_grid * (ctx->N + PART_EXTRA));
+    a.gpart = (float *)((gp + 15) & ~(uintptr_t)15);
+  }
   a.bar = ctx->bar;
   a.dstatus = ctx->dstatus;
   a.z_out = ctx->zact;
