@@ -18,7 +18,8 @@
 //            sums over CTAs -> grid barrier (deterministic, no float atomics)
 //   step     every CTA forms the same d = P+(y - s g) - y (second
 //            Barzilai-Borwein step s) from the same reduced gradient
-//   pass B   z = M y (refreshed exactly) and w = M d, thread per voxel
+//   pass B   w = M d, thread per voxel (z = M y recomputed exactly every 16th
+//            iteration; in between z is carried by the updates z += t w)
 //   search   phi'(t) = sum_j w_j F'(z_j + t w_j) + gamma*(dG(y).d + 2t G(d))
 //            is piecewise linear and nondecreasing: each round evaluates it
 //            at 16 points (FP32 per voxel, FP64 across warps and CTAs), one
@@ -915,11 +916,14 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[1] += c1 - s_clk[4]; s_clk[4] = c1; }
 
-    // ---------------- pass B: z = M y, w = M d
+    // ---------------- pass B: w = M d (and z = M y)
     // per own subtile, the thread streams its 16 bytes of each nonzero column
     // through a private ring of shared-memory slots (STG copies in flight;
     // the columns are mostly L2-resident, so latency bounds this pass)
+    // z itself is carried by the updates z += t w; every 16th iteration it is
+    // recomputed from y so that FP32 rounding cannot accumulate
     {
+      const bool refresh = (it & 15) == 0;
       constexpr int STG = master_pipe_stages(VPT);
       float4 *pipe = (float4 *)s_rows;  // [STG][nthr], slot k of thread t at k*nthr + t
 #pragma unroll
@@ -933,20 +937,35 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
           cp_async_commit();
         }
-        for (int q = 0; q < nm; ++q) {
-          cp_async_wait<STG - 1>();
-          const int slot = q & (STG - 1);
-          const float4 v = pipe[slot * nthr + tid];
-          const int sl = cl[q];
-          const float ys = s_yf[sl], ds = s_df[sl];
-          zz.x = fmaf(v.x, ys, zz.x); ww.x = fmaf(v.x, ds, ww.x);
-          zz.y = fmaf(v.y, ys, zz.y); ww.y = fmaf(v.y, ds, ww.y);
-          zz.z = fmaf(v.z, ys, zz.z); ww.z = fmaf(v.z, ds, ww.z);
-          zz.w = fmaf(v.w, ys, zz.w); ww.w = fmaf(v.w, ds, ww.w);
-          if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
-          cp_async_commit();
+        if (refresh) {
+          for (int q = 0; q < nm; ++q) {
+            cp_async_wait<STG - 1>();
+            const int slot = q & (STG - 1);
+            const float4 v = pipe[slot * nthr + tid];
+            const int sl = cl[q];
+            const float ys = s_yf[sl], ds = s_df[sl];
+            zz.x = fmaf(v.x, ys, zz.x); ww.x = fmaf(v.x, ds, ww.x);
+            zz.y = fmaf(v.y, ys, zz.y); ww.y = fmaf(v.y, ds, ww.y);
+            zz.z = fmaf(v.z, ys, zz.z); ww.z = fmaf(v.z, ds, ww.z);
+            zz.w = fmaf(v.w, ys, zz.w); ww.w = fmaf(v.w, ds, ww.w);
+            if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
+            cp_async_commit();
+          }
+          z[4 * m] = zz.x; z[4 * m + 1] = zz.y; z[4 * m + 2] = zz.z; z[4 * m + 3] = zz.w;
+        } else {
+          for (int q = 0; q < nm; ++q) {
+            cp_async_wait<STG - 1>();
+            const int slot = q & (STG - 1);
+            const float4 v = pipe[slot * nthr + tid];
+            const float ds = s_df[cl[q]];
+            ww.x = fmaf(v.x, ds, ww.x);
+            ww.y = fmaf(v.y, ds, ww.y);
+            ww.z = fmaf(v.z, ds, ww.z);
+            ww.w = fmaf(v.w, ds, ww.w);
+            if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
+            cp_async_commit();
+          }
         }
-        z[4 * m] = zz.x; z[4 * m + 1] = zz.y; z[4 * m + 2] = zz.z; z[4 * m + 3] = zz.w;
         w[4 * m] = ww.x; w[4 * m + 1] = ww.y; w[4 * m + 2] = ww.z; w[4 * m + 3] = ww.w;
       }
       cp_async_wait<0>();
