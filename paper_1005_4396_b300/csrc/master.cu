@@ -14,16 +14,22 @@
 //   pass A   gradient M^T F'(z): F' of the CTA's subtiles goes to shared
 //            memory; each warp streams whole (column, subtile) pairs with
 //            many independent 16-byte loads per lane
-//   reduce   per-slot CTA partials -> grid barrier -> warp-per-slot fixed-order
-//            sums over CTAs -> grid barrier (deterministic, no float atomics)
+//   reduce   per-slot CTA partials (FP32 rows) -> grid barrier -> every CTA
+//            sums all rows in the same fixed order, compensated (one barrier;
+//            deterministic, no float atomics)
 //   step     every CTA forms the same d = P+(y - s g) - y (second
 //            Barzilai-Borwein step s) from the same reduced gradient
-//   pass B   w = M d, thread per voxel (z = M y recomputed exactly every 16th
-//            iteration; in between z is carried by the updates z += t w)
+//   pass B   w = M d, thread per voxel, column segments streamed through a
+//            per-thread cp.async ring; z = M y is recomputed exactly only every
+//            16th iteration and otherwise carried by the updates z += t w: the
+//            iterates then stay consistent with the line that was searched,
+//            where a fresh FP32 product each iteration adds rounding noise to
+//            the gradient differences the Barzilai-Borwein step is made of
+//            (3x more iterations)
 //   search   phi'(t) = sum_j w_j F'(z_j + t w_j) + gamma*(dG(y).d + 2t G(d))
 //            is piecewise linear and nondecreasing: each round evaluates it
-//            at 16 points (FP32 per voxel, FP64 across warps and CTAs), one
-//            grid reduction per round; stop once Newton steps from both ends
+//            at 16 points (FP32 per voxel, compensated FP32 across warps and
+//            CTAs), one grid reduction per round; stop once Newton steps from both ends
 //            of the bracket agree (same linear piece: the secant is exact).
 // Stop: rho = max_k |min(y_k, g_k)| <= tol * max(rho_start, rho_ref).
 // The grid barrier is one counter whose top bit flips when every CTA has
