@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
-# current kernel (bench.py --case master: 8.215405 GB read + 7.696 MB written
+# current kernel (bench.py --case master: 8.222328 GB read + 5.677 MB written
 # for (2*30+2) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
 # to None whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = None  # kernel changed since the last capture
+MASTER_TRAFFIC_RATIO = (8.222328e9 + 5.677056e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 
