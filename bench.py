@@ -7,7 +7,7 @@ pricing -> aperture column -> master problem) on the prostate-scale phantom
 D).  value = column-generation iterations per second over all ranks, inputs
 resident in HBM.  Also reported: the roofline of the dominant kernel, the
 sparse products' HBM bandwidth, FP16/BF16-D plans with their dose error
-against the FP64 oracle, an end-to-end figure through the C-ABI from host
+against FP64 NumPy products of the same D, an end-to-end figure through the C-ABI from host
 buffers, and the oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -164,11 +164,74 @@ def _algorithmic_bytes(prob, info, rec):
             np.array(dense, dtype=np.float64))
 
 
+# ---------------------------------------------------------------- FP64 checks
+# Dose and gradient errors reported beside the timings are taken against
+# plain FP64 NumPy products of the same D (the library is not involved).
+def _fluence64(cfg, lleaf, rleaf, y):
+    """Beamlet fluence of apertures (open columns [l, r) of each row) with
+    intensities y: x_(k,row,c) = y_k where open (Eq. 3)."""
+    N, R, C = cfg.n_angles, cfg.n_rows, cfg.n_cols
+    c = np.arange(C).reshape(1, 1, C)
+    l = np.asarray(lleaf, np.int64).reshape(N, R, 1)
+    r = np.asarray(rleaf, np.int64).reshape(N, R, 1)
+    return (((c >= l) & (c < r)) * np.asarray(y, np.float64).reshape(N, 1, 1)).reshape(-1)
+
+
+def _dose64(prob, x):
+    """z_j = sum_i D_ij x_i in FP64."""
+    w = np.repeat(np.asarray(x, np.float64), np.diff(prob.row_ptr)) * prob.val
+    return np.bincount(prob.vox_idx, weights=w, minlength=prob.n_vox)
+
+
+def _price64(prob, f):
+    """g_i = sum_j D_ij f_j in FP64 (empty rows give 0)."""
+    prod = prob.val * np.asarray(f, np.float64)[prob.vox_idx]
+    g = np.zeros(prob.n_beamlets)
+    nz = np.flatnonzero(np.diff(prob.row_ptr) > 0)
+    g[nz] = np.add.reduceat(prod, prob.row_ptr[nz])
+    return g
+
+
+def _cost64(prob, z):
+    """sum_j F(z_j) (Eq. 1) and F'(z) in FP64."""
+    Tv, av, bv = prob.voxel_params()
+    e = z - Tv
+    return float(np.sum(np.where(e > 0, bv, av) * e * e)), np.where(e > 0, 2 * bv * e, 2 * av * e)
+
+
+def _gaps(theta, cyclic):
+    """(left, right) neighbour and gap of each beam on the arc (None at path ends)."""
+    n = len(theta)
+    out = []
+    for k in range(n):
+        lft = k - 1 if k > 0 else (n - 1 if cyclic and n > 1 else None)
+        rgt = k + 1 if k < n - 1 else (0 if cyclic and n > 1 else None)
+        gl = None if lft is None else (theta[k] - theta[lft] if lft < k else theta[0] + 360.0 - theta[n - 1])
+        gr = None if rgt is None else (theta[rgt] - theta[k] if rgt > k else theta[0] + 360.0 - theta[n - 1])
+        out.append((lft, gl, rgt, gr))
+    return out
+
+
+def _rate64(theta, y, cyclic):
+    """Largest |y_k' - y_k| / gap over neighbouring beams (degrees)."""
+    return max([abs(y[r] - y[k]) / g for k, (_, _, r, g) in enumerate(_gaps(theta, cyclic)) if r is not None],
+               default=0.0)
+
+
+def _dG64(theta, y, cyclic):
+    """Gradient of the smoothing term of Eq. 2."""
+    g = np.zeros(len(y))
+    for k, (lft, gl, rgt, gr) in enumerate(_gaps(theta, cyclic)):
+        if lft is not None:
+            g[k] += 2.0 * (y[k] - y[lft]) / gl
+        if rgt is not None:
+            g[k] -= 2.0 * (y[rgt] - y[k]) / gr
+    return g
+
+
 def _dose_err(prob, plan_f, plan_ref_dose, lleaf, rleaf, y):
     """max/mean |z - z_FP64| over voxels, in % of the largest prescription."""
-    import oracle
-    x = oracle.aperture_fluence(prob.cfg, lleaf, rleaf, y)
-    z64 = oracle.dose(prob, x)
+    z64 = _dose64(prob, _fluence64(prob.cfg, lleaf, rleaf, y))
     d = np.abs(plan_ref_dose.astype(np.float64) - z64)
     rx = float(prob.T.max())
     return float(d.max() / rx * 100), float(d.mean() / rx * 100)
@@ -300,6 +363,7 @@ def run_ours(args):
 
     if rank == 0 and ws == 1 and not args.quick:
         out["variants"] = run_variants(prob, plan, recs[-1], kkt)  # reads this plan's state first
+        out["dose_rate_feasibility"] = run_feasibility(prob, plan, recs[-1], kkt)
         if args.master == "pg":
             out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
         out["e2e"] = run_e2e(prob, args)
@@ -311,10 +375,28 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_feasibility(prob, plan, rec, kkt):
+    """Sec. 3 final step on the timed plan: a dose-rate limit of half the
+    plan's largest variation between neighbours (the paper gives no value),
+    gamma doubled per round until the plan meets it."""
+    cfg = prob.cfg
+    y = rec["y"]
+    top = _rate64(prob.theta_deg, y, cfg.cyclic)
+    limit = 0.5 * top
+    t0 = time.perf_counter()
+    r = plan.dose_rate_feasibility(limit, gamma_factor=2.0, max_rounds=30, kkt_tol=kkt,
+                                   allow_infeasible=True)
+    dt = time.perf_counter() - t0
+    return {"limit_per_degree": limit, "largest_before": top, "rounds": r["rounds"],
+            "gamma": r["gamma"], "violation_after": r["violation"], "feasible": r["violation"] <= 0,
+            "cost_before": float(rec["cost"][-1]), "cost_after": r["cost"], "ms": round(dt * 1e3, 2),
+            "note": "limit proposed here (half the plan's largest |dy|/gap); cost_after uses the final gamma"}
+
+
 def run_newton(prob, plan, rec_pg, kkt, args):
     """The same plan with the projected-Newton master (an option beyond the
     paper): CG iterations/s, master iterations and where the time goes; its
-    plan's dose against the FP64 oracle for the same apertures and
+    plan's dose against the FP64 dose (NumPy) of the same apertures and
     intensities."""
     import torch
     plan.set_master_method("newton")
@@ -352,7 +434,7 @@ def run_newton(prob, plan, rec_pg, kkt, args):
 
 
 def run_variants(prob, plan32, rec32, kkt=1e-6):
-    """FP16-D and BF16-D plans: throughput and dose error against the FP64 oracle."""
+    """FP16-D and BF16-D plans: throughput and dose error against an FP64 product of D."""
     import torch
     from paper_1005_4396_b300 import vmat
     res = {}
@@ -379,7 +461,7 @@ def run_variants(prob, plan32, rec32, kkt=1e-6):
                        "final_cost": float(r["cost"][-1]),
                        "beams_in_same_order_as_f32": same,
                        "device_bytes": p.info["device_bytes"]}
-    res["note"] = ("dose error: the plan's own dose on the GPU against the FP64 oracle's dose of "
+    res["note"] = ("dose error: the plan's own dose on the GPU against the FP64 dose (NumPy) of "
                    "the same apertures and intensities, % of the largest prescription")
     return res
 
@@ -488,13 +570,11 @@ def run_batched(args):
     batch.run(kkt_tol=kkt)  # warm-up replay
     outs, plan_ms, total_ms = batch.run(kkt_tol=kkt)
     errs = []
-    import oracle
     for prob, plan, out in zip(probs, plans16, outs):
         if prob is None:
             continue
         z = plan.plan_dose().cpu().numpy()
-        x = oracle.aperture_fluence(prob.cfg, out["lleaf"], out["rleaf"], out["y"])
-        z64 = oracle.dose(prob, x)
+        z64 = _dose64(prob, _fluence64(prob.cfg, out["lleaf"], out["rleaf"], out["y"]))
         errs.append(float(np.abs(z - z64).max() / prob.T.max() * 100))
     n = len(plans16)
     iters = sum(c.n_angles for c in cfgs)
@@ -524,21 +604,19 @@ def run_autograd(args):
     per call (U(0,1), 288,000 beamlets) forward + hand-written backward, and
     32 aperture-intensity vectors through random deliverable-shaped apertures;
     throughput in vectors/s with CUDA events, and sampled errors against the
-    FP64 oracle gradient and central differences of the oracle cost
-    (h = 1e-3, 8 directions normalised to |d|_inf = 1)."""
+    FP64 gradient and central differences of the FP64 cost (h = 1e-3, 8
+    directions normalised to |d|_inf = 1)."""
     import torch
     from paper_1005_4396_b300 import autograd, inputs, vmat
-    import oracle
     torch.cuda.set_device(0)
     prob = inputs.make_problem(inputs.prostate_config())
     cfg = prob.cfg
-    sid, T, al, be = prob.struct_id, prob.T, prob.alpha, prob.beta
 
     def ocost(x):
-        return oracle.voxel_cost(oracle.dose(prob, x), sid, T, al, be)
+        return _cost64(prob, _dose64(prob, x))[0]
 
     def ograd(x):
-        return oracle.price(prob, oracle.voxel_dcost(oracle.dose(prob, x), sid, T, al, be))
+        return _price64(prob, _cost64(prob, _dose64(prob, x))[1])
 
     def rel(a, b):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
@@ -579,7 +657,7 @@ def run_autograd(args):
         step_x()
         gx = X.grad.cpu().numpy()
         x = Xh[:, 5].astype(np.float64)
-        out["fluence"]["rel_err_vs_oracle_grad"] = rel(gx[:, 5], ograd(x))
+        out["fluence"]["rel_err_vs_fp64_grad"] = rel(gx[:, 5], ograd(x))
         dirs = inputs.rng.normal(94, 8 * prob.n_beamlets).reshape(8, prob.n_beamlets)
         dirs /= np.abs(dirs).max(axis=1, keepdims=True)
         h = 1e-3
@@ -588,10 +666,12 @@ def run_autograd(args):
         step_y()
         gy = Y.grad.cpu().numpy()
         y = Yh[:, 2].astype(np.float64)
-        xf = oracle.aperture_fluence(cfg, l, r, y)
-        g_or = oracle.aperture_adjoint(cfg, l, r, ograd(xf)) + \
-            cfg.gamma * oracle.dG(prob.theta_deg, y, cfg.cyclic)
-        out["intensity"]["rel_err_vs_oracle_grad"] = rel(gy[:, 2], g_or)
+        N, R, C = cfg.n_angles, cfg.n_rows, cfg.n_cols
+        xf = _fluence64(cfg, l, r, y)
+        openm = _fluence64(cfg, l, r, np.ones(N)).reshape(N, R * C)
+        g_or = (openm * ograd(xf).reshape(N, R * C)).sum(axis=1) + \
+            cfg.gamma * _dG64(prob.theta_deg, y, cfg.cyclic)
+        out["intensity"]["rel_err_vs_fp64_grad"] = rel(gy[:, 2], g_or)
     out["note"] = ("one call = forward dose+cost of 32 vectors and the backward of their sum; "
                    "errors: relative 2-norm on one sampled vector")
     print(json.dumps(out), flush=True)

@@ -276,6 +276,28 @@ typedef enum {
 } vmat_master_method;
 VMAT_API vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method);
 
+/* Dose-rate feasibility of the final plan (Sec. 3).  Eq. 2 only penalises
+ * the dose-rate variation between neighbouring beams; as a hard limit the
+ * paper raises gamma and re-optimises the intensities of the final apertures
+ * until the plan is feasible.  Feasible: for every pair of neighbouring beams
+ * (the wrap pair too when cyclic; beams without an aperture count with y = 0)
+ * |y_k' - y_k| / gap <= max_rate, gap in degrees.  The paper gives no limit:
+ * max_rate (intensity units per degree, >= 0) is the caller's.  Each round
+ * multiplies gamma by gamma_factor (> 1) and solves the master problem again
+ * from the current y (gradient-projection or projected-Newton method as set,
+ * kkt_tol and the plan's reference residual as in vmat_colgen_run), at most
+ * max_rounds rounds (0: only check).  Out (each may be NULL): y_host [N]
+ * final intensities (also the plan's y), gamma_out the final gamma,
+ * rounds_out rounds taken, violation_out max over pairs of |dy|/gap -
+ * max_rate (<= 0 when feasible), cost_out Eq. 3 at the end with the final
+ * gamma.  The context keeps its own gamma.  VMAT_ENOTCONV if the limit is
+ * still exceeded after max_rounds (outputs written). */
+VMAT_API vmat_status vmat_dose_rate_feasibility(vmat_ctx *ctx, double max_rate, double gamma_factor,
+                                                int32_t max_rounds, int32_t master_max_iters,
+                                                double kkt_tol, double *y_host, double *gamma_out,
+                                                int32_t *rounds_out, double *violation_out,
+                                                double *cost_out);
+
 /* ---- many independent plans (planning throughput; not in the paper) ----
  * A batch groups existing contexts (not owned).  Every plan's master kernel
  * gets a CTA budget (its SM "tokens"); a list schedule decides which plans

@@ -280,3 +280,52 @@ def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricin
         raise RuntimeError(f"oracle colgen failed: {rc}")
     rec.update(y=y, z=z, lleaf=lleaf, rleaf=rleaf)
     return rec
+
+
+# ---------------------------------------------------------------- dose-rate feasibility (Sec. 3)
+def rate_violation(theta, y, max_rate, cyclic=True) -> float:
+    """Largest dose-rate variation over neighbouring beams, |y_k' - y_k| / gap
+    (gap in degrees, the wrap pair included on a ring), minus max_rate."""
+    theta, y = _f64(theta), _f64(y)
+    n = y.size
+    if n < 2:
+        return -float(max_rate)
+    worst = -np.inf
+    pairs = [(k, k + 1) for k in range(n - 1)] + ([(n - 1, 0)] if cyclic else [])
+    for k, kp in pairs:
+        gap = theta[kp] - theta[k] if kp > k else theta[0] + 360.0 - theta[n - 1]
+        worst = max(worst, abs(y[kp] - y[k]) / gap - max_rate)
+    return float(worst)
+
+
+def dose_rate_feasibility(prob, col_beam, lleaf, rleaf, y0, max_rate, gamma_factor=2.0,
+                          max_rounds=20, eps=1e-8, rho_ref=0.0, max_iter=100000):
+    """Sec. 3, final step: the smoothing term of Eq. 2 is a soft penalty; to
+    meet a hard limit on the dose-rate variation the weight gamma is raised
+    and the intensities of the final apertures re-optimised (master problem,
+    warm start from the last y) until the plan is feasible.  Each round
+    multiplies gamma by gamma_factor.  Returns dict(y, gamma, rounds,
+    violation, cost, G) with cost = Eq. 3 at the end (final gamma) and G the
+    smoothing term of each round's solution (round 0: the starting y)."""
+    cfg = prob.cfg
+    R = cfg.n_rows
+    col_beam = np.asarray(col_beam, dtype=np.int32)
+    M = np.array([aperture_dose(prob, k, lleaf[k * R:(k + 1) * R], rleaf[k * R:(k + 1) * R])
+                  for k in col_beam])
+    theta = prob.theta_deg
+    gamma = cfg.gamma
+    y = _f64(y0).copy()
+    v = rate_violation(theta, y, max_rate, cfg.cyclic)
+    Gs = [G(theta, y, cfg.cyclic)]
+    rounds = 0
+    while v > 0.0 and rounds < max_rounds:
+        gamma *= gamma_factor
+        rounds += 1
+        res = master(M, col_beam, theta, prob.struct_id, prob.T, prob.alpha, prob.beta, gamma,
+                     cfg.cyclic, y, eps=eps, max_iter=max_iter, rho_ref=rho_ref)
+        y = res["y"]
+        v = rate_violation(theta, y, max_rate, cfg.cyclic)
+        Gs.append(G(theta, y, cfg.cyclic))
+    z = M.T @ y[col_beam]
+    cost = voxel_cost(z, prob.struct_id, prob.T, prob.alpha, prob.beta) + gamma * G(theta, y, cfg.cyclic)
+    return dict(y=y, gamma=gamma, rounds=rounds, violation=v, cost=cost, G=np.array(Gs))

@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "vmat_internal.cuh"
 
 vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
@@ -121,6 +123,78 @@ extern "C" vmat_status vmat_master_step(vmat_ctx *ctx, int32_t max_iters, double
   if (o.status == VMAT_ETIMEOUT) return vmat_fail(ctx, VMAT_ETIMEOUT, "master: bounded wait ran out");
   if (o.status != VMAT_OK)
     return vmat_fail(ctx, VMAT_ENOTCONV, "master: rho %.3e after %d iterations", o.rho, o.iters);
+  return VMAT_OK;
+}
+
+// Largest dose-rate variation over neighbouring beams with an aperture or
+// without (y = 0 there), |y_k' - y_k| / gap(k, k') in intensity units per
+// degree, minus the limit: <= 0 when the plan meets it.
+static double rate_violation(const vmat_ctx *ctx, const std::vector<double> &y, double max_rate) {
+  const int N = ctx->N;
+  double worst = -INFINITY;
+  for (int k = 0; k + 1 < N || (ctx->cyclic && N > 1 && k < N); ++k) {
+    const int kp = k + 1 < N ? k + 1 : 0;
+    if (kp == k) break;
+    const double gap = kp > k ? ctx->theta_h[kp] - ctx->theta_h[k]
+                              : ctx->theta_h[0] + 360.0 - ctx->theta_h[N - 1];
+    worst = fmax(worst, fabs(y[kp] - y[k]) / gap - max_rate);
+  }
+  return N > 1 ? worst : -max_rate;
+}
+
+extern "C" vmat_status vmat_dose_rate_feasibility(vmat_ctx *ctx, double max_rate, double gamma_factor,
+                                                  int32_t max_rounds, int32_t master_max_iters,
+                                                  double kkt_tol, double *y_host, double *gamma_out,
+                                                  int32_t *rounds_out, double *violation_out,
+                                                  double *cost_out) {
+  if (!ctx) return VMAT_EINVAL;
+  if (!(max_rate >= 0.0) || !isfinite(max_rate) || !(gamma_factor > 1.0) || !isfinite(gamma_factor) ||
+      max_rounds < 0 || master_max_iters < 0 || !(kkt_tol >= 0.0))
+    return vmat_fail(ctx, VMAT_EINVAL,
+                     "max_rate >= 0, gamma_factor > 1, max_rounds >= 0, master_max_iters >= 0 and "
+                     "kkt_tol >= 0 required");
+  const int N = ctx->N;
+  std::vector<double> y(N);
+  VMAT_CUDA(ctx, cudaMemcpyAsync(y.data(), ctx->y, N * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  vmat_status s = sync_status(ctx);
+  if (s != VMAT_OK) return s;
+  const double gamma0 = ctx->gamma;
+  double v = rate_violation(ctx, y, max_rate);
+  int rounds = 0;
+  MasterOut o = {};
+  // the cost at the current plan (a master launch of no iterations), then one
+  // master solve per round with gamma raised, warm-started from the last y
+  for (;;) {
+    const bool more = v > 0.0 && rounds < max_rounds;
+    if (more) {
+      ctx->gamma *= gamma_factor;
+      ++rounds;
+    }
+    s = vmat_launch_master(ctx, more ? master_max_iters : 0, kkt_tol, 0.0, 0, nullptr, nullptr,
+                           nullptr, nullptr);
+    if (s == VMAT_OK) {
+      VMAT_CUDA(ctx, cudaMemcpyAsync(&o, ctx->mout, sizeof o, cudaMemcpyDeviceToHost, ctx->stream));
+      VMAT_CUDA(ctx, cudaMemcpyAsync(y.data(), ctx->y, N * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      s = sync_status(ctx);
+    }
+    if (s == VMAT_OK && o.status == VMAT_ETIMEOUT)
+      s = vmat_fail(ctx, VMAT_ETIMEOUT, "master: bounded wait ran out");
+    if (s != VMAT_OK) {
+      ctx->gamma = gamma0;
+      return s;
+    }
+    v = rate_violation(ctx, y, max_rate);
+    if (!more) break;
+  }
+  if (y_host) std::copy(y.begin(), y.end(), y_host);
+  if (gamma_out) *gamma_out = ctx->gamma;
+  if (rounds_out) *rounds_out = rounds;
+  if (violation_out) *violation_out = v;
+  if (cost_out) *cost_out = o.cost_active + ctx->inactive_cost + ctx->gamma * o.smooth;
+  ctx->gamma = gamma0;
+  if (v > 0.0)
+    return vmat_fail(ctx, VMAT_ENOTCONV, "dose-rate limit still exceeded by %.3e after %d rounds", v,
+                     rounds);
   return VMAT_OK;
 }
 

@@ -389,6 +389,7 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   VMAT_CUDA(ctx, cudaMemcpyAsync(ctx->tabd, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st));
   VMAT_CUDA(ctx, cudaMemcpyAsync(ctx->tabf, tabf.data(), tabf.size() * 4, cudaMemcpyHostToDevice, st));
   VMAT_CUDA(ctx, cudaMemcpyAsync(ctx->theta, P->theta_deg, ctx->N * 8, cudaMemcpyHostToDevice, st));
+  ctx->theta_h.assign(P->theta_deg, P->theta_deg + ctx->N);
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->sid_full, V));
   VMAT_CUDA(ctx, cudaMemcpyAsync(ctx->sid_full, P->struct_id, V, cudaMemcpyHostToDevice, st));
 

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/vmat.h"
 
@@ -52,6 +53,7 @@ struct vmat_ctx {
   float *tabf = nullptr;       // [3*256] T, alpha, beta (float)
   double *tabd = nullptr;      // [3*256] T, alpha, beta (double)
   double *theta = nullptr;     // [N]
+  std::vector<double> theta_h; // [N] host copy (dose-rate limits between neighbours)
   float *scale = nullptr;      // [B] per-beamlet scale of reduced-precision D (1 for F32)
   int64_t *bm_ptr = nullptr;   // [B+1] beamlet-major CSR over active voxels
   int32_t *bm_col = nullptr;

@@ -98,6 +98,7 @@ EXPORTS = {
     "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
     "vmat_set_master_method": [_p, _i32],
+    "vmat_dose_rate_feasibility": [_p, _d, _d, _i32, _i32, _d, _p, _p, _p, _p, _p],
 }
 
 _lib = None
@@ -383,6 +384,9 @@ class Plan:
     def reset(self):
         vmat_reset(self.ctx)
 
+    def dose_rate_feasibility(self, max_rate, **kw):
+        return vmat_dose_rate_feasibility(self.ctx, self.cfg.n_angles, max_rate, **kw)
+
     def set_master_method(self, method):
         """'pg' (the paper's gradient projection, default) or 'newton'."""
         vmat_set_master_method(self.ctx, method)
@@ -423,6 +427,23 @@ MASTER_METHODS = {"pg": VMAT_MASTER_PROJECTED_GRADIENT, "newton": VMAT_MASTER_PR
 
 def vmat_set_master_method(ctx, method):
     _check(ctx, load_library().vmat_set_master_method(ctx, int(MASTER_METHODS.get(method, method))))
+
+
+def vmat_dose_rate_feasibility(ctx, n_angles, max_rate, gamma_factor=2.0, max_rounds=20,
+                               master_max_iters=100000, kkt_tol=1e-6, allow_infeasible=False):
+    """Sec. 3 final step: raise gamma and re-optimise y until every neighbour
+    pair has |dy|/gap <= max_rate.  Returns dict(y, gamma, rounds, violation,
+    cost, status)."""
+    y = np.zeros(n_angles)
+    g, v, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    r = ctypes.c_int32()
+    st = load_library().vmat_dose_rate_feasibility(ctx, float(max_rate), float(gamma_factor),
+                                                   int(max_rounds), int(master_max_iters),
+                                                   float(kkt_tol), y.ctypes.data, ctypes.byref(g),
+                                                   ctypes.byref(r), ctypes.byref(v), ctypes.byref(c))
+    if st != VMAT_OK and not (allow_infeasible and st == VMAT_ENOTCONV):
+        _check(ctx, st)
+    return dict(y=y, gamma=g.value, rounds=r.value, violation=v.value, cost=c.value, status=st)
 
 
 def vmat_set_master_budget(ctx, max_ctas):
