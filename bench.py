@@ -677,6 +677,51 @@ def run_autograd(args):
     print(json.dumps(out), flush=True)
 
 
+def run_coarse(args):
+    """Coarse voxels for unspecified tissue (Sec. 3): the plan optimised on
+    the problem whose tissue voxels are merged in 2x2x2 blocks (volume-
+    weighted), against the plan optimised at full resolution; both evaluated
+    at full resolution (FP64 NumPy dose of each plan's fluence)."""
+    import torch
+    from paper_1005_4396_b300 import inputs, vmat
+    torch.cuda.set_device(0)
+    cfg = _workload(args.workload)
+    fine = inputs.make_problem(cfg)
+    t0 = time.perf_counter()
+    cp = inputs.coarse_tissue(fine)
+    t_merge = time.perf_counter() - t0
+    kkt = max(cfg.kkt_eps, 1e-6)
+    res = {}
+    for name, prob in (("full", fine), ("coarse_tissue", cp.prob)):
+        with vmat.Plan(prob, val_f32=True) as plan:
+            for _ in range(args.warmup):
+                plan.reset()
+                plan.colgen_run(kkt_tol=kkt)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            plan.reset()
+            a.record()
+            r = plan.colgen_run(kkt_tol=kkt)
+            b.record()
+            torch.cuda.synchronize()
+            s = a.elapsed_time(b) / 1e3
+            info = plan.info
+        z = _dose64(fine, _fluence64(cfg, r["lleaf"], r["rleaf"], r["y"]))
+        c = _cost64(fine, z)[0]
+        Gy = float(np.sum([(r["y"][k2] - r["y"][k]) ** 2 / g for k, (_, _, k2, g) in
+                           enumerate(_gaps(fine.theta_deg, cfg.cyclic)) if k2 is not None]))
+        res[name] = {"s_per_plan": round(s, 4), "cg_iters_per_s": round(len(r["k"]) / s, 2),
+                     "active_voxels": info["n_active"], "nnz": prob.nnz,
+                     "master_iters": int(r["iters"].sum()),
+                     "full_resolution_cost": c + cfg.gamma * Gy}
+    out = {"metric": "CG iters/s with coarse tissue voxels, full-resolution cost of the plan",
+           "value": res["coarse_tissue"]["cg_iters_per_s"], "unit": UNIT, "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": _describe(cfg, fine)}, "merge_s": round(t_merge, 2), **res,
+           "cost_ratio_coarse_over_full": res["coarse_tissue"]["full_resolution_cost"] /
+           res["full"]["full_resolution_cost"]}
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- profiling cases
 def run_case(args):
     """Small cases sized for an ncu capture (a few GB on the device, inputs
@@ -761,11 +806,16 @@ def main():
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--master", default="pg", choices=["pg", "newton"],
                     help="master method of the timed plan (pg: the paper's gradient projection)")
+    ap.add_argument("--coarse", action="store_true",
+                    help="coarse tissue voxels (2x2x2) against full resolution, evaluated at full resolution")
     ap.add_argument("--autograd", action="store_true",
                     help="the differentiable dose+cost (32 vectors per call) on the prostate phantom")
     args = ap.parse_args()
     if args.autograd:
         run_autograd(args)
+        return
+    if args.coarse:
+        run_coarse(args)
         return
     if args.case:
         run_case(args)

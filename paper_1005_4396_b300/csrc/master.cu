@@ -1232,8 +1232,9 @@ static cudaError_t master_occupancy_any(int vpt, bool newton, int nthr, size_t s
 
 // Launch shape: the fewest voxels per thread (4, 8, 16, 32) that fit the
 // SMs with 512-thread CTAs, then threads per CTA chosen so that about
-// MASTER_CTA_TARGET CTAs cover the voxels (512 threads from 16 voxels per
-// thread on: there the extra warps hide more latency than fewer CTAs save).  Fewer, larger CTAs make the grid
+// MASTER_CTA_TARGET CTAs cover the voxels, but never fewer than 256 threads
+// (small problems then take fewer CTAs: 8 warps per CTA hide the pass
+// latencies that 2-5 warps do not) and 512 from 16 voxels per thread on.  Fewer, larger CTAs make the grid
 // barriers and cross-CTA sums of every iteration cheaper; on B300 ~110 CTAs
 // still stream the columns at full bandwidth, while more voxels per thread
 // (16, 32) lengthen every per-voxel pass.
@@ -1248,7 +1249,7 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   if (vpt > 32) return vmat_fail(ctx, VMAT_EINVAL, "too many active voxels for the master kernel");
   const int64_t per = (Va + (int64_t)vpt * target - 1) / ((int64_t)vpt * target);
   int nthr = (int)(((per + 31) / 32) * 32);
-  if (nthr < 64) nthr = 64;
+  if (nthr < 256) nthr = 256;  // small problems: fewer CTAs of at least 8 warps
   if (nthr > 512 || vpt >= 16) nthr = 512;  // at 16+ voxels per thread every warp counts
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);

@@ -356,3 +356,72 @@ def random_apertures(seed: int, cfg: PlanConfig, stream: int = 1):
                 a = b = (a + b) // 2
             l[k, row], r[k, row] = a, b
     return l.astype(np.int16).ravel(), r.astype(np.int16).ravel()
+
+
+# --------------------------------------------------------------------------
+# coarse voxels for unspecified tissue (Sec. 3)
+# --------------------------------------------------------------------------
+@dataclass
+class CoarseProblem:
+    """A problem whose unspecified-tissue voxels are merged in 2x2x2 blocks.
+    fine_to: [V_fine] index of each fine voxel's voxel in `prob`; weight:
+    [V] fine voxels represented (1 for kept voxels, 1..8 for merged
+    tissue).  Volume weighting rides on the structures: a merged voxel of
+    weight w gets a structure with (T, w alpha, w beta) of tissue, so that
+    Eq. 1 summed over the coarse voxels counts every fine voxel once."""
+    prob: Problem
+    fine_to: np.ndarray
+    weight: np.ndarray
+
+
+def coarse_tissue(prob: Problem, tissue_sid: int = 1) -> CoarseProblem:
+    """Merge the tissue voxels (structure `tissue_sid`) of each 2x2x2 block of
+    the grid into one voxel whose D row is the mean of its members' rows (a
+    member with no entry counts as 0); every other voxel is kept.  Kept
+    voxels come first in grid order, then one voxel per block with tissue,
+    in block order."""
+    cfg = prob.cfg
+    nx, ny, nz = cfg.nx, cfg.ny, cfg.nz
+    V = prob.n_vox
+    j = np.arange(V)
+    ix, iy, iz = j % nx, (j // nx) % ny, j // (nx * ny)
+    bx, by = (nx + 1) // 2, (ny + 1) // 2
+    block = ((iz // 2) * by + iy // 2) * bx + ix // 2
+    tissue = prob.struct_id == tissue_sid
+    kept = np.flatnonzero(~tissue)
+    fine_to = np.empty(V, np.int64)
+    fine_to[kept] = np.arange(kept.size)
+    ublocks, binv, bcount = np.unique(block[tissue], return_inverse=True, return_counts=True)
+    fine_to[tissue] = kept.size + binv
+    Vc = kept.size + ublocks.size
+    weight = np.ones(Vc, np.int64)
+    weight[kept.size:] = bcount
+    # structures: the original ones, then tissue with weight 2..8 (weight 1 keeps tissue_sid)
+    n_s = prob.T.size
+    sid = np.empty(Vc, np.uint8)
+    sid[:kept.size] = prob.struct_id[kept]
+    wc = weight[kept.size:]
+    sid[kept.size:] = np.where(wc == 1, tissue_sid, n_s + wc - 2).astype(np.uint8)
+    ws = np.arange(2, 9)
+    T = np.concatenate([prob.T, np.full(7, prob.T[tissue_sid])])
+    alpha = np.concatenate([prob.alpha, ws * prob.alpha[tissue_sid]])
+    beta = np.concatenate([prob.beta, ws * prob.beta[tissue_sid]])
+    names = list(prob.struct_names) + [f"tissue x{w}" for w in ws]
+    # D rows: map voxels, scale merged entries by 1/weight, sum duplicates per row
+    B = prob.n_beamlets
+    rows = np.repeat(np.arange(B, dtype=np.int64), np.diff(prob.row_ptr))
+    cols = fine_to[prob.vox_idx]
+    vals = prob.val / weight[cols]
+    key = rows * Vc + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    first = np.concatenate([[True], key[1:] != key[:-1]])
+    starts = np.flatnonzero(first)
+    vals = np.add.reduceat(vals, starts)
+    key = key[starts]
+    rows, cols = key // Vc, key % Vc
+    row_ptr = np.zeros(B + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=B), out=row_ptr[1:])
+    coarse = Problem(cfg=cfg, theta_deg=prob.theta_deg, struct_id=sid, T=T, alpha=alpha, beta=beta,
+                     row_ptr=row_ptr, vox_idx=cols.astype(np.int32), val=vals, struct_names=names)
+    return CoarseProblem(prob=coarse, fine_to=fine_to, weight=weight)
