@@ -363,6 +363,7 @@ def run_ours(args):
 
     if rank == 0 and ws == 1 and not args.quick:
         out["variants"] = run_variants(prob, plan, recs[-1], kkt)  # reads this plan's state first
+        out["plan_quality"] = run_quality(prob, plan)  # before the feasibility step changes y
         out["dose_rate_feasibility"] = run_feasibility(prob, plan, recs[-1], kkt)
         if args.master == "pg":
             out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
@@ -373,6 +374,26 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_quality(prob, plan):
+    """Dose-volume histograms of the timed plan (GPU, 1500 bins up to 1.5 x
+    the largest prescription) and per-structure figures (mean, D95, D5,
+    fraction at or above the largest prescription)."""
+    import torch
+    from paper_1005_4396_b300 import quality
+    rx = float(prob.T.max())
+    z = plan.plan_dose()
+    plan.dvh(z, 1.5 * rx, 1500)  # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    counts = plan.dvh(z, 1.5 * rx, 1500)
+    b.record()
+    torch.cuda.synchronize()
+    m = quality.dvh_metrics(counts, 1.5 * rx, prob.struct_names, rx)
+    return {"dvh_ms": round(a.elapsed_time(b), 3), "prescription": rx,
+            "structures": {k: {q: round(v, 4) if isinstance(v, float) else v for q, v in d.items()}
+                           for k, d in m.items() if k != "air"}}
 
 
 def run_feasibility(prob, plan, rec, kkt):

@@ -298,6 +298,17 @@ VMAT_API vmat_status vmat_dose_rate_feasibility(vmat_ctx *ctx, double max_rate, 
                                                 int32_t *rounds_out, double *violation_out,
                                                 double *cost_out);
 
+/* Plan quality (the evaluation behind Fig. 2; not part of the optimisation):
+ * dose-volume histogram counts per structure of a dose vector z_dev [n_vox]
+ * float on the device (e.g. from vmat_plan_dose).  Voxel j goes to bin
+ * floor(z_j * s) of its structure, s = n_bins / dose_max rounded to FP32
+ * once, the product in FP32, clamped to [0, n_bins - 1] (the last bin holds
+ * doses >= dose_max too).  counts_host [n_struct * n_bins] int64, structure
+ * major, host memory; exact integer counts.  VMAT_EINVAL for dose_max <= 0,
+ * n_bins outside 1..4096, or more than 24,576 structure bins in all. */
+VMAT_API vmat_status vmat_dvh(vmat_ctx *ctx, const float *z_dev, double dose_max, int32_t n_bins,
+                              int64_t *counts_host);
+
 /* ---- many independent plans (planning throughput; not in the paper) ----
  * A batch groups existing contexts (not owned).  Every plan's master kernel
  * gets a CTA budget (its SM "tokens"); a list schedule decides which plans

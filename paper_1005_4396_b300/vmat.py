@@ -98,6 +98,7 @@ EXPORTS = {
     "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
     "vmat_set_master_method": [_p, _i32],
+    "vmat_dvh": [_p, _p, _d, _i32, _p],
     "vmat_dose_rate_feasibility": [_p, _d, _d, _i32, _i32, _d, _p, _p, _p, _p, _p],
 }
 
@@ -384,6 +385,11 @@ class Plan:
     def reset(self):
         vmat_reset(self.ctx)
 
+    def dvh(self, z, dose_max, n_bins=1000):
+        import torch
+        _require_cuda(z, torch.float32, self.prob.n_vox, "z")
+        return vmat_dvh(self.ctx, z, self.prob.T.size, dose_max, n_bins)
+
     def dose_rate_feasibility(self, max_rate, **kw):
         return vmat_dose_rate_feasibility(self.ctx, self.cfg.n_angles, max_rate, **kw)
 
@@ -444,6 +450,13 @@ def vmat_dose_rate_feasibility(ctx, n_angles, max_rate, gamma_factor=2.0, max_ro
     if st != VMAT_OK and not (allow_infeasible and st == VMAT_ENOTCONV):
         _check(ctx, st)
     return dict(y=y, gamma=g.value, rounds=r.value, violation=v.value, cost=c.value, status=st)
+
+
+def vmat_dvh(ctx, z, n_struct, dose_max, n_bins=1000):
+    """Per-structure dose histogram counts [n_struct, n_bins] of the device dose z."""
+    counts = np.zeros(n_struct * n_bins, np.int64)
+    _check(ctx, load_library().vmat_dvh(ctx, _ptr(z), float(dose_max), int(n_bins), counts.ctypes.data))
+    return counts.reshape(n_struct, n_bins)
 
 
 def vmat_set_master_budget(ctx, max_ctas):
