@@ -62,13 +62,13 @@ def lib():
             "vo_leaf_limits": (None, [_c_i32] * 5 + [_p, _p, _p, _c_i32, _p, _p, _p, _p]),
             "vo_row_scan": (_c_i32, [_c_i32, _p, _c_i32, _c_i32, _c_i32, _c_i32, _p, _p, _p]),
             "vo_row_scan_f32": (_c_i32, [_c_i32, _p, _c_i32, _c_i32, _c_i32, _c_i32, _p, _p, _p]),
-            "vo_pricing": (_c_i32, [_c_i32] * 5 + [_p, _p, _p, _p, _c_i32, _p, _p, _p, _p, _p, _p]),
+            "vo_pricing": (_c_i32, [_c_i32] * 5 + [_p, _p, _p, _p, _c_i32, _p, _p, _p, _p, _p, _p, _p]),
             "vo_line_search": (_c_d, [_c_i64, _p, _p, _p, _p, _p, _p, _c_d, _c_d, _c_d]),
             "vo_master": (_c_i32, [_c_i64, _c_i32, _p, _p, _c_i32, _p, _c_i32, _c_d, _p, _p, _p,
                                    _p, _c_d, _c_d, _c_i32, _p, _p, _p]),
             "vo_colgen": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32, _p, _p, _p, _p, _p, _p, _p,
                                    _p, _c_d, _c_i32, _c_i32, _c_i32, _c_d, _c_i32, _p, _p, _p,
-                                   _c_i32] + [_p] * 12),
+                                   _c_i32, _c_i32] + [_p] * 12),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -193,8 +193,11 @@ def row_scan(g, Llo, Lhi, Rlo, Rhi, f32=False):
     return None if rc != 0 else (v.value, l.value, r.value)
 
 
-def pricing(cfg, occ, lleaf, rleaf, g, f32=False, N=None, R=None, C=None, s=None, cyclic=None):
+def pricing(cfg, occ, lleaf, rleaf, g, f32=False, N=None, R=None, C=None, s=None, cyclic=None,
+            offset=None):
     """Pricing subproblem over beams without an aperture (Sec. 2.2).
+    offset [N]: added to each beam's aperture price (None: the beamlet sum
+    alone); smoothing_offset() gives the one of the exact reduced cost.
     Returns dict(k, l, r, p, p2, row_margin) or raises on failure."""
     N = cfg.n_angles if N is None else N
     R = cfg.n_rows if R is None else R
@@ -211,12 +214,21 @@ def pricing(cfg, occ, lleaf, rleaf, g, f32=False, N=None, R=None, C=None, s=None
     p = ctypes.c_double()
     p2 = ctypes.c_double()
     rm = ctypes.c_double()
+    off = None if offset is None else _f64(offset)
+    if off is not None and off.size != N:
+        raise ValueError("offset must have one value per beam")
     rc = lib().vo_pricing(N, R, C, s, int(cyclic), _ptr(occ), _ptr(lleaf), _ptr(rleaf), _ptr(g),
                           int(f32), ctypes.byref(k), _ptr(lo), _ptr(ro), ctypes.byref(p),
-                          ctypes.byref(p2), ctypes.byref(rm))
+                          ctypes.byref(p2), ctypes.byref(rm), _ptr(off))
     if rc != 0:
         raise RuntimeError(f"oracle pricing failed: {rc}")
     return dict(k=k.value, l=lo, r=ro, p=p.value, p2=p2.value, row_margin=rm.value)
+
+
+def smoothing_offset(theta, y, gamma, cyclic=True) -> np.ndarray:
+    """gamma * dG/dy at y (Eq. 2): for a beam without an aperture (y_k = 0)
+    the smoothing part of the derivative of Eq. 3 along its new column."""
+    return gamma * dG(theta, y, cyclic)
 
 
 # ---------------------------------------------------------------- master
@@ -248,9 +260,12 @@ def master(M, col_beam, theta, sid, T, alpha, beta, gamma, cyclic, y0, eps=1e-8,
 
 
 # ---------------------------------------------------------------- column generation
-def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricing=False):
+def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricing=False,
+           price_smoothing=False):
     """Column generation (Sec. 2.2, Fig. 1) from an empty plan.
     forced: optional (k [n_iter], l [n_iter, R], r [n_iter, R]) to replay.
+    price_smoothing: price each beam by the exact reduced cost (beamlet sum
+    plus gamma dG/dy_k at the current y) instead of the beamlet sum alone.
     Returns a dict of per-iteration records and the final plan."""
     cfg = prob.cfg
     N, R, C = cfg.n_angles, cfg.n_rows, cfg.n_cols
@@ -273,7 +288,7 @@ def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricin
         prob.n_vox, N, R, C, _ptr(prob.row_ptr), _ptr(prob.vox_idx), _ptr(prob.val),
         _ptr(prob.struct_id), _ptr(T), _ptr(alpha), _ptr(beta), _ptr(theta), cfg.gamma,
         int(cfg.cyclic), cfg.max_leaf_step, n_iter, eps, max_iter, _ptr(fk), _ptr(fl), _ptr(fr),
-        int(f32_pricing), _ptr(rec["k"]), _ptr(rec["p"]), _ptr(rec["margin"]),
+        int(f32_pricing), int(price_smoothing), _ptr(rec["k"]), _ptr(rec["p"]), _ptr(rec["margin"]),
         _ptr(rec["row_margin"]), _ptr(rec["cost"]), _ptr(rec["rho"]), _ptr(rec["iters"]),
         _ptr(rec["status"]), _ptr(y), _ptr(z), _ptr(lleaf), _ptr(rleaf))
     if rc != 0:

@@ -258,10 +258,14 @@ static double row_runner_up(int C, const double *g, int Llo, int Lhi, int Rlo, i
  * Outputs: k*, its leaves l/r [R], p*, the second-least price p2 (INFINITY
  * if only one candidate), and the least row margin (runner-up value minus
  * chosen value over the rows of k*, FP64 enumeration; NULL to skip).
+ * offset [N] (NULL: none) is added to each beam's price after the row sum:
+ * the column generation passes gamma * dG/dy_k of Eq. 2 at the current y for
+ * the exact reduced cost of a new column (see vo_colgen).
  * Returns 0, -1 if no beam is free, -2 if some free beam has an infeasible row. */
 int vo_pricing(int N, int R, int C, int s, int cyclic, const uint8_t *occ, const int16_t *lleaf,
                const int16_t *rleaf, const double *g, int f32, int *kstar, int16_t *lout,
-               int16_t *rout, double *pstar, double *p2, double *row_margin) {
+               int16_t *rout, double *pstar, double *p2, double *row_margin,
+               const double *offset) {
   int *Llo = malloc(sizeof(int) * R * 4);
   int *Lhi = Llo + R, *Rlo = Llo + 2 * R, *Rhi = Llo + 3 * R;
   float *gf = malloc(sizeof(float) * C);
@@ -286,6 +290,7 @@ int vo_pricing(int N, int R, int C, int s, int cyclic, const uint8_t *occ, const
       if (rc != 0) { status = -2; goto done; }
       p += v;
     }
+    if (offset) p += offset[k];
     if (best < 0 || p < bp) {
       if (best >= 0) second = bp;
       best = k; bp = p;
@@ -522,13 +527,19 @@ int vo_master(int64_t V, int ncol, const double *M, const int32_t *col_beam, int
  * rho <= eps * max(rho_start, rho_plan), rho_plan = the residual at the start
  * of the first one.  Final y [N], z [V], leaves
  * lleaf/rleaf [N*R] (rows of beams without an aperture are 0).
+ * price_smoothing != 0 prices a beam by the exact reduced cost of its new
+ * column: the derivative of Eq. 3 along it is the summed beamlet price of
+ * the aperture plus gamma * dG/dy_k at the current y (y_k = 0 for a beam
+ * without an aperture, so the term is -2 gamma times the neighbours'
+ * intensities over their gaps, never positive); otherwise the aperture price
+ * is the beamlet sum alone, as the paper states it.
  * Returns 0, or a negative pricing status. */
 int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int32_t *vox,
               const double *val, const uint8_t *sid, const double *T, const double *al,
               const double *be, const double *theta, double gamma, int cyclic, int s,
               int n_iter, double eps, int max_iter, const int32_t *forced_k,
               const int16_t *forced_l, const int16_t *forced_r, int f32_pricing,
-              int32_t *rec_k, double *rec_p, double *rec_margin, double *rec_row_margin,
+              int price_smoothing, int32_t *rec_k, double *rec_p, double *rec_margin, double *rec_row_margin,
               double *rec_cost, double *rec_rho, int32_t *rec_iters, int32_t *rec_status,
               double *y, double *z, int16_t *lleaf, int16_t *rleaf) {
   const int64_t B = (int64_t)N * R * C;
@@ -537,6 +548,7 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
   uint8_t *occ = calloc(N, 1), *mask = malloc(N);
   double *fp = malloc(sizeof(double) * V), *g = calloc(B, sizeof(double));
   int16_t *lk = malloc(sizeof(int16_t) * R), *rk = malloc(sizeof(int16_t) * R);
+  double *off = malloc(sizeof(double) * N);
   int status = 0;
   double rho_plan = 0.0;
   for (int k = 0; k < N; ++k) y[k] = 0.0;
@@ -549,8 +561,12 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
     vo_price(B, R * C, row_ptr, vox, val, fp, mask, g);
     int k;
     double p, p2, rm;
+    if (price_smoothing) {
+      vo_dG(N, theta, y, cyclic, off);
+      for (int q = 0; q < N; ++q) off[q] *= gamma;
+    }
     int rc = vo_pricing(N, R, C, s, cyclic, occ, lleaf, rleaf, g, f32_pricing, &k, lk, rk, &p,
-                        &p2, &rm);
+                        &p2, &rm, price_smoothing ? off : NULL);
     if (rc != 0) { status = rc; break; }
     double scale = fabs(p) > 1e-300 ? fabs(p) : 1e-300;
     rec_p[t] = p;
@@ -577,5 +593,6 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
     rec_iters[t] = (int32_t)out[3];
   }
   free(M); free(col_beam); free(occ); free(mask); free(fp); free(g); free(lk); free(rk);
+  free(off);
   return status;
 }

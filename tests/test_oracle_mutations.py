@@ -25,6 +25,12 @@ MUTATIONS = {
     "line search wrong curvature": ("Bc += 2.0 * c * wj * wj;", "Bc += c * wj * wj;"),
     "master ignores smoothing in gradient": ("grad[k] *= gamma;", "grad[k] *= 0.0;"),
     "aperture dose includes right leaf": ("for (int c = l[rr]; c < r[rr]; ++c) {", "for (int c = l[rr]; c <= r[rr] && c < C; ++c) {"),
+    "smoothing price offset sign": ("for (int q = 0; q < N; ++q) off[q] *= gamma;",
+                                    "for (int q = 0; q < N; ++q) off[q] *= -gamma;",
+                                    "test_oracle_price_smoothing.py"),
+    "smoothing price offset of the next beam": ("if (offset) p += offset[k];",
+                                                "if (offset) p += offset[(k + 1) % N];",
+                                                "test_oracle_price_smoothing.py"),
 }
 
 RUNNER = r"""
@@ -41,7 +47,8 @@ sys.exit(pytest.main([{tests!r}, "-x", "-q", "-p", "no:cacheprovider"]))
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name):
-    old, new = MUTATIONS[name]
+    old, new, *pins = MUTATIONS[name]
+    pins = pins[0] if pins else "test_oracle.py"
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old}"
     with tempfile.TemporaryDirectory() as d:
@@ -51,6 +58,6 @@ def test_planted_mistake_is_caught(name):
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                "-ffp-contract=off", msrc, "-o", mlib, "-lm"])
         code = RUNNER.format(root=ROOT, lib=mlib, src=msrc,
-                             tests=os.path.join(ROOT, "tests", "test_oracle.py"))
+                             tests=os.path.join(ROOT, "tests", pins))
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
