@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import dataclasses
 import ctypes
 import io
 import json
@@ -365,6 +366,7 @@ def run_ours(args):
         out["variants"] = run_variants(prob, plan, recs[-1], kkt)  # reads this plan's state first
         out["plan_quality"] = run_quality(prob, plan)  # before the feasibility step changes y
         out["dose_rate_feasibility"] = run_feasibility(prob, plan, recs[-1], kkt)
+        out["price_smoothing"] = run_price_smoothing(prob, plan, recs[-1], kkt)
         if args.master == "pg":
             out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
         out["e2e"] = run_e2e(prob, args)
@@ -412,6 +414,85 @@ def run_feasibility(prob, plan, rec, kkt):
             "gamma": r["gamma"], "violation_after": r["violation"], "feasible": r["violation"] <= 0,
             "cost_before": float(rec["cost"][-1]), "cost_after": r["cost"], "ms": round(dt * 1e3, 2),
             "note": "limit proposed here (half the plan's largest |dy|/gap); cost_after uses the final gamma"}
+
+
+def _plan_parts(prob, r):
+    """Eq. 1 voxel cost (FP64 NumPy dose of the plan's fluence), Eq. 2
+    smoothing term and largest |dy|/gap of a finished plan, on its own arc."""
+    cfg = prob.cfg
+    y = r["y"]
+    z = _dose64(prob, _fluence64(cfg, r["lleaf"], r["rleaf"], y))
+    G = float(np.sum([(y[k2] - y[k]) ** 2 / g for k, (_, _, k2, g) in
+                      enumerate(_gaps(prob.theta_deg, cfg.cyclic)) if k2 is not None]))
+    return {"voxel_cost": _cost64(prob, z)[0], "G": G, "max_rate_per_degree": _rate64(prob.theta_deg, y, cfg.cyclic)}
+
+
+def _timed_plan(plan, kkt):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.reset()
+    torch.cuda.synchronize()
+    a.record()
+    r = plan.colgen_run(kkt_tol=kkt)
+    b.record()
+    torch.cuda.synchronize()
+    return r, a.elapsed_time(b) / 1e3
+
+
+def run_price_smoothing(prob, plan, rec, kkt):
+    """The timed plan again with smoothing-aware pricing: each beam priced by
+    the exact reduced cost of its new column (beamlet sum + gamma dG/dy_k,
+    an option; the paper prices by the beamlet sum)."""
+    plan.set_price_smoothing(True)
+    try:
+        r, s = _timed_plan(plan, kkt)
+    finally:
+        plan.set_price_smoothing(False)
+    n = len(r["k"])
+    return {"cg_iters_per_s": round(n / s, 3), "s_per_plan": round(s, 4),
+            "master_iters": int(r["iters"].sum()), "final_cost": float(r["cost"][-1]),
+            "final_cost_literal_pricing": float(rec["cost"][-1]),
+            "iterations_with_other_beam": int(np.sum(r["k"] != rec["k"])),
+            "note": "option beyond the paper's literal price; same workload and KKT rule"}
+
+
+def run_study(args):
+    """Pricing study on one workload: the paper's literal aperture price
+    against the exact reduced cost (smoothing derivative included), on a ring
+    of beams (the smoothing and leaf-travel neighbours wrap around, as the
+    arc of a full rotation) and on a path (Eq. 2 as printed, k = 1..N-1).
+    Each plan is evaluated in FP64 on its own arc."""
+    import torch
+    from paper_1005_4396_b300 import inputs, vmat
+    torch.cuda.set_device(0)
+    cfg = _workload(args.workload)
+    base = inputs.make_problem(cfg)
+    kkt = max(cfg.kkt_eps, 1e-6)
+    rows = []
+    for cyclic in (True, False):
+        prob = inputs.Problem(**{**base.__dict__, "cfg": dataclasses.replace(cfg, cyclic=cyclic)})
+        with vmat.Plan(prob, val_f32=True) as plan:
+            for _ in range(args.warmup if cyclic else 1):
+                plan.reset()
+                plan.colgen_run(kkt_tol=kkt)
+            for exact in (False, True):
+                plan.set_price_smoothing(exact)
+                r, s = _timed_plan(plan, kkt)
+                parts = _plan_parts(prob, r)
+                rows.append({"arc": "ring" if cyclic else "path",
+                             "pricing": "exact reduced cost" if exact else "beamlet sum (paper)",
+                             "s_per_plan": round(s, 4), "cg_iters_per_s": round(len(r["k"]) / s, 3),
+                             "master_iters": int(r["iters"].sum()),
+                             "final_cost": float(r["cost"][-1]),
+                             "voxel_cost": round(parts["voxel_cost"], 6),
+                             "gamma_G": round(cfg.gamma * parts["G"], 6),
+                             "max_rate_per_degree": round(parts["max_rate_per_degree"], 6),
+                             "beam_order_head": r["k"][:8].tolist()})
+    out = {"metric": "pricing study: CG iters/s and final cost, literal vs exact reduced-cost pricing, ring vs path",
+           "value": rows[0]["cg_iters_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic", "config": {"workload": _describe(cfg, base)},
+           "gamma": cfg.gamma, "plans": rows}
+    print(json.dumps(out), flush=True)
 
 
 def run_newton(prob, plan, rec_pg, kkt, args):
@@ -831,7 +912,12 @@ def main():
                     help="coarse tissue voxels (2x2x2) against full resolution, evaluated at full resolution")
     ap.add_argument("--autograd", action="store_true",
                     help="the differentiable dose+cost (32 vectors per call) on the prostate phantom")
+    ap.add_argument("--study", default=None, choices=["pricing"],
+                    help="pricing: literal vs exact reduced-cost pricing on a ring and on a path of beams")
     args = ap.parse_args()
+    if args.study:
+        run_study(args)
+        return
     if args.autograd:
         run_autograd(args)
         return

@@ -276,6 +276,19 @@ typedef enum {
 } vmat_master_method;
 VMAT_API vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method);
 
+/* Price of a beam in the pricing subproblem (Sec. 2.2).  on = 0 (default):
+ * the least summed beamlet price of a feasible aperture, as the paper states
+ * it.  on = 1: that sum plus gamma * dG/dy_k of Eq. 2 at the current y, which
+ * makes it the exact reduced cost (the derivative of Eq. 3 along the new
+ * column): for a beam without an aperture (y_k = 0) the added term is
+ * -2 gamma (y_{k-1} / gap_left + y_{k+1} / gap_right), gaps in degrees, the
+ * wrap pair on a ring, computed in FP64 and added after the row sum.  The
+ * aperture of each beam is unchanged (the term is constant per beam); only
+ * the choice of beam and the recorded prices change.  Read by every pricing
+ * enqueued after the call (a batch re-captures its graph when it changes).
+ * VMAT_EINVAL unless on is 0 or 1. */
+VMAT_API vmat_status vmat_set_price_smoothing(vmat_ctx *ctx, int32_t on);
+
 /* Dose-rate feasibility of the final plan (Sec. 3).  Eq. 2 only penalises
  * the dose-rate variation between neighbouring beams; as a hard limit the
  * paper raises gamma and re-optimises the intensities of the final apertures
@@ -348,7 +361,9 @@ VMAT_API vmat_status vmat_list_schedule(int32_t n, const int32_t *budget, const 
 /* Run every plan's full column generation (one aperture per beam) from an
  * empty plan as one graph launch.  res [n_plans] as for vmat_colgen_run
  * (phase_ms unused), plan_ms [n_plans] time from the launch to each plan's
- * end, total_ms the whole launch (either may be NULL). */
+ * end, total_ms the whole launch (either may be NULL).  The graph is captured
+ * on the first run and again whenever the arguments or a plan's settings
+ * (gamma, master method, smoothing-aware pricing) changed since. */
 VMAT_API vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_iters, double kkt_tol,
                                            vmat_colgen_result *res, double *plan_ms,
                                            double *total_ms);

@@ -32,6 +32,7 @@ struct vmat_batch {
   cudaGraphExec_t exec = nullptr;
   int g_iters = -2, g_trial = -2;
   double g_kkt = -1.0;
+  std::vector<double> g_sig;  // per-plan settings the graph was captured with
   std::vector<Records> rec;
   char *rec_block = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_start = nullptr, ev_stop = nullptr;
@@ -216,6 +217,17 @@ extern "C" vmat_status vmat_batch_configure(vmat_batch *b, int32_t share) {
 
 // Capture every plan (reset + iterations) into one graph: each plan on its
 // own stream, after the fork and after the plans whose tokens it takes over.
+// Settings of each plan that its captured launches bake in as arguments.
+static std::vector<double> plan_settings(const vmat_batch *b) {
+  std::vector<double> v;
+  for (const vmat_ctx *c : b->plans) {
+    v.push_back(c->gamma);
+    v.push_back(c->master_method);
+    v.push_back(c->price_smoothing);
+  }
+  return v;
+}
+
 static vmat_status build_graph(vmat_batch *b, int trial, int master_max_iters, double kkt) {
   drop_graph(b);
   cudaStream_t o = b->origin;
@@ -255,6 +267,7 @@ static vmat_status build_graph(vmat_batch *b, int trial, int master_max_iters, d
   b->g_iters = master_max_iters;
   b->g_kkt = kkt;
   b->g_trial = trial;
+  b->g_sig = plan_settings(b);
   return VMAT_OK;
 }
 
@@ -318,7 +331,8 @@ extern "C" vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_i
     vmat_status s = vmat_batch_configure(b, 1);
     if (s != VMAT_OK) return s;
   }
-  if (!b->exec || b->g_iters != master_max_iters || b->g_kkt != kkt_tol || b->g_trial != 0) {
+  if (!b->exec || b->g_iters != master_max_iters || b->g_kkt != kkt_tol || b->g_trial != 0 ||
+      b->g_sig != plan_settings(b)) {
     vmat_status s = build_graph(b, 0, master_max_iters, kkt_tol);
     if (s != VMAT_OK) return s;
   }

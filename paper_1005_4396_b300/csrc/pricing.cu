@@ -7,7 +7,9 @@
 // pass over its C beamlets: P[0] = 0, P[c+1] = P[c] + g_c in FP32; for each
 // r the best left leaf is the feasible l of largest P[l] (ties: largest l);
 // the row keeps the least P[r] - P[l], then the shortest interval, then the
-// smallest l.  The aperture price sums the row values in FP64, row order.
+// smallest l.  The aperture price sums the row values in FP64, row order;
+// with smoothing-aware pricing it then adds gamma * dG/dy_k of Eq. 2 at the
+// current y (the exact reduced cost of the new column, see smoothing_slope).
 // A row is tiny (C <= 128) and its sequential order fixes ties exactly, so
 // the scan stays sequential per thread; all rows of a beam run in parallel.
 // k_select: least aperture price over free beams (ties: lowest beam), and
@@ -19,12 +21,38 @@
 
 #include "vmat_internal.cuh"
 
+// dG/dy_k of Eq. 2 at y: the pair (k-1, k) contributes 2 (y_k - y_{k-1}) / gap,
+// the pair (k, k+1) -2 (y_{k+1} - y_k) / gap (on a ring the wrap pair joins
+// beams N-1 and 0, gap theta_0 + 360 - theta_{N-1}); the two are combined as
+// (0 + left) - right, each rounded once, FP64.  A beam without an aperture
+// has y_k = 0, so this is -2 times its neighbours' intensities over the gaps.
+__device__ __forceinline__ double smoothing_slope(const double *__restrict__ y,
+                                                  const double *__restrict__ theta, int N,
+                                                  int cyclic, int k) {
+  if (N < 2) return 0.0;
+  double out = 0.0;
+  if (k > 0 || cyclic) {
+    const int a = k > 0 ? k - 1 : N - 1;
+    const double gap = a + 1 < N ? theta[a + 1] - theta[a] : theta[0] + 360.0 - theta[N - 1];
+    out = __dadd_rn(out, __ddiv_rn(__dmul_rn(2.0, __dsub_rn(y[k], y[a])), gap));
+  }
+  if (k < N - 1 || cyclic) {
+    const int b = k + 1 < N ? k + 1 : 0;
+    const double gap = k + 1 < N ? theta[k + 1] - theta[k] : theta[0] + 360.0 - theta[N - 1];
+    out = __dsub_rn(out, __ddiv_rn(__dmul_rn(2.0, __dsub_rn(y[b], y[k])), gap));
+  }
+  return out;
+}
+
 __global__ void __launch_bounds__(128) k_pricing(const float *__restrict__ g,
                                                  const uint8_t *__restrict__ occ,
                                                  const int16_t *__restrict__ lleaf,
                                                  const int16_t *__restrict__ rleaf, int N, int R,
                                                  int C, int s, int cyclic, double *ap_price,
-                                                 int16_t *ap_l, int16_t *ap_r) {
+                                                 int16_t *ap_l, int16_t *ap_r,
+                                                 const double *__restrict__ y,
+                                                 const double *__restrict__ theta, double gamma,
+                                                 int smooth) {
   const int k = blockIdx.x;
   __shared__ int nb[2], dist[2];
   __shared__ float rowv[VMAT_MAX_ROWS];
@@ -95,6 +123,7 @@ __global__ void __launch_bounds__(128) k_pricing(const float *__restrict__ g,
       ok &= rowok[row];
       p += (double)rowv[row];
     }
+    if (smooth) p = __dadd_rn(p, __dmul_rn(smoothing_slope(y, theta, N, cyclic, k), gamma));
     ap_price[k] = ok ? p : NAN;
   }
 }
@@ -172,7 +201,8 @@ vmat_status vmat_launch_pricing_rec(vmat_ctx *ctx, const float *g, int32_t *rec_
                                     double *rec_p2) {
   k_pricing<<<ctx->N, 64, 0, ctx->stream>>>(g, ctx->occ, ctx->lleaf, ctx->rleaf, ctx->N, ctx->R,
                                             ctx->C, ctx->step, ctx->cyclic, ctx->ap_price,
-                                            ctx->ap_l, ctx->ap_r);
+                                            ctx->ap_l, ctx->ap_r, ctx->y, ctx->theta, ctx->gamma,
+                                            ctx->price_smoothing);
   k_select<<<1, 256, 0, ctx->stream>>>(ctx->ap_price, ctx->occ, ctx->ap_l, ctx->ap_r, ctx->N,
                                        ctx->R, ctx->sel, ctx->sel_l, ctx->sel_r, rec_k, rec_p,
                                        rec_p2);

@@ -354,6 +354,14 @@ extern "C" vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method) {
   return VMAT_OK;
 }
 
+extern "C" vmat_status vmat_set_price_smoothing(vmat_ctx *ctx, int32_t on) {
+  if (!ctx) return VMAT_EINVAL;
+  if (on != 0 && on != 1) return vmat_fail(ctx, VMAT_EINVAL, "price_smoothing must be 0 or 1");
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->price_smoothing = on;
+  return VMAT_OK;
+}
+
 static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_t st,
                                vmat_ctx *ctx) {
   Tmp tmp;

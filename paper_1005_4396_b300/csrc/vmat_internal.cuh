@@ -43,6 +43,7 @@ struct vmat_ctx {
   vmat_dtype dt = VMAT_F32;
   double gamma = 0.0;
   int32_t cyclic = 1, step = 1;
+  int32_t price_smoothing = 0;  // 1: pricing adds gamma dG/dy_k (exact reduced cost)
   double inactive_cost = 0.0;  // sum of F(0) over voxels D never reaches
 
   // problem on the device

@@ -98,6 +98,7 @@ EXPORTS = {
     "vmat_batch_colgen_run": [_p, _i32, _d, _p, _p, _p],
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
     "vmat_set_master_method": [_p, _i32],
+    "vmat_set_price_smoothing": [_p, _i32],
     "vmat_dvh": [_p, _p, _d, _i32, _p],
     "vmat_dose_rate_feasibility": [_p, _d, _d, _i32, _i32, _d, _p, _p, _p, _p, _p],
 }
@@ -397,6 +398,11 @@ class Plan:
         """'pg' (the paper's gradient projection, default) or 'newton'."""
         vmat_set_master_method(self.ctx, method)
 
+    def set_price_smoothing(self, on=True):
+        """Price beams by the exact reduced cost (beamlet sum + gamma dG/dy_k)
+        instead of the beamlet sum alone (the default, as in the paper)."""
+        vmat_set_price_smoothing(self.ctx, on)
+
     def set_profiling(self, on=True):
         vmat_set_profiling(self.ctx, on)
 
@@ -433,6 +439,10 @@ MASTER_METHODS = {"pg": VMAT_MASTER_PROJECTED_GRADIENT, "newton": VMAT_MASTER_PR
 
 def vmat_set_master_method(ctx, method):
     _check(ctx, load_library().vmat_set_master_method(ctx, int(MASTER_METHODS.get(method, method))))
+
+
+def vmat_set_price_smoothing(ctx, on):
+    _check(ctx, load_library().vmat_set_price_smoothing(ctx, int(bool(on))))
 
 
 def vmat_dose_rate_feasibility(ctx, n_angles, max_rate, gamma_factor=2.0, max_rounds=20,
