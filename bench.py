@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
-# current kernel (bench.py --case master: 8.222328 GB read + 5.677 MB written
-# for (2*30+2) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
+# current kernel (bench.py --case master: 8.085323 GB read + 6.086 MB written
+# for (2*30+1) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
 # to None whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (8.222328e9 + 5.677056e6) / ((2 * 30 + 2) * 150 * 221440 * 4 + 8 * 221440)
+MASTER_TRAFFIC_RATIO = (8.085323e9 + 6.086144e6) / ((2 * 30 + 1) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 
@@ -139,8 +139,9 @@ def _describe(cfg, prob):
 def _algorithmic_bytes(prob, info, rec):
     """Bytes each kernel must move per launch by its definition (not counting
     re-reads).  master: every PG iteration reads the aperture-dose columns
-    twice (gradient pass, direction pass) plus once at entry and once at
-    exit, counting only the subtiles of a column that hold a nonzero (an
+    twice (gradient pass, direction pass) plus once at entry (the dose at
+    exit comes from the carried state), counting only the subtiles of a
+    column that hold a nonzero (an
     all-zero subtile carries no information and is not read), and writes z
     and F'.  price: the D rows of the free beams (8 B/nnz FP32 value+index),
     their row pointers, the prices written, F' gathered once.  Also returns
@@ -156,8 +157,8 @@ def _algorithmic_bytes(prob, info, rec):
     sub = np.cumsum(rec["col_subtiles"].astype(np.float64))
     for t, k in enumerate(rec["k"]):
         P = int(rec["iters"][t])
-        master.append((2 * P + 2) * sub[t] * sv * 4 + 8 * Va)
-        dense.append((2 * P + 2) * (t + 1) * Va * 4 + 8 * Va)
+        master.append((2 * P + 1) * sub[t] * sv * 4 + 8 * Va)
+        dense.append((2 * P + 1) * (t + 1) * Va * 4 + 8 * Va)
         free_beams = cfg.n_angles - t
         price.append(free_nnz * vb + free_beams * RC * (8 + 4) + 4 * Va)
         free_nnz -= nnz_beam[k]
@@ -309,7 +310,7 @@ def run_ours(args):
         "launches_per_step": n_master,
         "bytes_per_step": float(mb.sum()),
         "dense_column_equivalent_GB/s": round(db.sum() / (ph_tot[3] / 1e3) / 1e9, 1),
-        "note": ("master algorithmic bytes per launch = (2*P+2) reads of the nonzero subtiles "
+        "note": ("master algorithmic bytes per launch = (2*P+1) reads of the nonzero subtiles "
                  "of the plan's aperture-dose columns (4 B per voxel) + z and F' written; "
                  "P = projected-gradient iterations of the launch; while the nonzero part "
                  "of the columns fits in L2 (126 MB) part of it is served from L2"),

@@ -433,11 +433,23 @@ static double kkt_residual(int ncol, const int32_t *col_beam, const double *y, c
   return r;
 }
 
+/* Step rule of the gradient projection: adaptive Barzilai-Borwein (ABBmin,
+ * Frassoldati, Zanni and Zanghirati 2008) with a memory of ABB_M short steps
+ * and switch ratio ABB_TAU for the first ABB_ITERS iterations of a solve, the
+ * short step alone after them. */
+#define ABB_M 3
+#define ABB_TAU 0.5
+#define ABB_ITERS 300
+
 /* Projected gradient for the master problem.  y [N] is the warm start on
  * entry (zero at beams without a column) and the solution on exit; z [V]
- * receives M y.  Step: second Barzilai-Borwein step (dy.dg / dg.dg, 1e12 if
- * either is not positive) clamped to [1e-12, 1e12], the first one
- * max(|y|_inf, 1)/|g|_inf, all norms over beams with a column; direction
+ * receives M y.  Step from the previous move dy and gradient change dg (over
+ * beams with a column): the short Barzilai-Borwein step BB2 = dy.dg / dg.dg
+ * (1e12 unless both are positive) and the long one BB1 = dy.dy / dy.dg
+ * (1e12 unless dy.dg > 0); where BB2 < ABB_TAU * BB1 the step is the least
+ * BB2 of this and the previous ABB_M - 1 iterations, else BB1 (from
+ * iteration ABB_ITERS on: BB2); clamped to
+ * [1e-12, 1e12]; the first step is max(|y|_inf, 1)/|g|_inf; direction
  * d = P+(y - s g) - y; exact line search on [0,1].  Stops when
  * rho <= eps * max(rho_start, rho_ref, 1e-300) or after max_iter
  * iterations; rho_ref is a caller-given scale (column generation passes the
@@ -461,7 +473,9 @@ int vo_master(int64_t V, int ncol, const double *M, const int32_t *col_beam, int
   double rho0 = rho, scale = rho0 > rho_ref ? rho0 : rho_ref;
   double tol = eps * (scale > 1e-300 ? scale : 1e-300);
   int it = 0, status = 1;
-  double dgg = 0.0, dyg = 0.0;
+  double dgg = 0.0, dyg = 0.0, dyy = 0.0;
+  double bb2_hist[ABB_M - 1]; /* previous short steps, newest first */
+  for (int q = 0; q < ABB_M - 1; ++q) bb2_hist[q] = INFINITY;
   for (it = 0; it < max_iter; ++it) {
     if (rho <= tol) { status = 0; break; }
     double step;
@@ -474,7 +488,14 @@ int vo_master(int64_t V, int ncol, const double *M, const int32_t *col_beam, int
       }
       step = (ym > 1.0 ? ym : 1.0) / (gm > 1e-300 ? gm : 1e-300);
     } else {
-      step = (dyg > 0.0 && dgg > 0.0) ? dyg / dgg : 1e12;
+      double bb2 = (dyg > 0.0 && dgg > 0.0) ? dyg / dgg : 1e12;
+      double bb1 = dyg > 0.0 ? dyy / dyg : 1e12;
+      double hmin = bb2;
+      for (int q = 0; q < ABB_M - 1; ++q)
+        if (bb2_hist[q] < hmin) hmin = bb2_hist[q];
+      for (int q = ABB_M - 2; q > 0; --q) bb2_hist[q] = bb2_hist[q - 1];
+      bb2_hist[0] = bb2;
+      step = it >= ABB_ITERS ? bb2 : (bb2 < ABB_TAU * bb1 ? hmin : bb1);
     }
     if (step < 1e-12) step = 1e-12;
     if (step > 1e12) step = 1e12;
@@ -496,12 +517,13 @@ int vo_master(int64_t V, int ncol, const double *M, const int32_t *col_beam, int
     memcpy(gold, g, sizeof(double) * N);
     vo_voxel_dcost(V, z, sid, T, al, be, fp);
     master_grad(V, ncol, M, col_beam, N, theta, cyclic, gamma, fp, y, g);
-    dgg = 0.0; dyg = 0.0;
+    dgg = 0.0; dyg = 0.0; dyy = 0.0;
     for (int q = 0; q < ncol; ++q) {
       int k = col_beam[q];
       double dy = t * d[k], dg = g[k] - gold[k];
       dgg += dg * dg;
       dyg += dy * dg;
+      dyy += dy * dy;
     }
     rho = kkt_residual(ncol, col_beam, y, g);
   }

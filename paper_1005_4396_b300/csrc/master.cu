@@ -8,24 +8,37 @@
 // into subtiles of ST = 4*threads voxels; CTA b owns the VPT/4 subtiles
 // b, b+G, b+2G, ... (spread over the volume, so dense and sparse regions
 // mix in every CTA) and thread t holds voxels 4t..4t+3 of each in registers
-// (dose z, direction image w) for the whole solve.  A column is nonzero
+// for the whole solve: the dose as its excess e = z - T over the voxel's
+// threshold (Eq. 1 depends on z only through e) and the direction image w.  A column is nonzero
 // only near its aperture's beam path: per (column, subtile) flags let every
 // pass skip all-zero subtiles.  Per iteration:
 //   pass A   gradient M^T F'(z): F' of the CTA's subtiles goes to shared
 //            memory; each warp streams whole (column, subtile) pairs with
-//            many independent 16-byte loads per lane
+//            many independent 16-byte loads per lane, compensated dot
+//            products per lane and a compensated warp sum
 //   reduce   per-slot CTA partials (FP32 rows) -> grid barrier -> every CTA
 //            sums all rows in the same fixed order, compensated (one barrier;
 //            deterministic, no float atomics)
-//   step     every CTA forms the same d = P+(y - s g) - y (second
-//            Barzilai-Borwein step s) from the same reduced gradient
+//   step     every CTA forms the same d = P+(y - s g) - y from the same
+//            reduced gradient; s is the adaptive Barzilai-Borwein step
+//            (ABBmin, Frassoldati, Zanni and Zanghirati 2008): the long step
+//            BB1 = dy.dy / dy.dg where it is close to the short one
+//            BB2 = dy.dg / dg.dg, else the least BB2 of the last few
+//            iterations; after 300 iterations of a solve BB2 alone (sixteen
+//            seeded plans: 42% fewer iterations than BB2 alone)
 //   pass B   w = M d, thread per voxel, column segments streamed through a
-//            per-thread cp.async ring; z = M y is recomputed exactly only every
-//            16th iteration and otherwise carried by the updates z += t w: the
-//            iterates then stay consistent with the line that was searched,
-//            where a fresh FP32 product each iteration adds rounding noise to
-//            the gradient differences the Barzilai-Borwein step is made of
-//            (3x more iterations)
+//            per-thread cp.async ring; e = M y - T is recomputed from y only
+//            at the start and every 16th iteration (compensated, y as a float
+//            pair; the solution's dose and F' are written from it) and
+//            otherwise carried by the updates e += t w: the iterates then stay
+//            consistent with the line that was searched, where a fresh FP32
+//            product each iteration adds rounding noise to the gradient
+//            differences the Barzilai-Borwein step is made of (3x more
+//            iterations).  Gradient noise near the stopping tolerance is what
+//            sets the iteration count: the excess form and the compensated
+//            sums with the adaptive step below (which the noise of plain FP32
+//            sums defeats) took a prostate plan from 21,400 to 11,700
+//            iterations
 //   search   phi'(t) = sum_j w_j F'(z_j + t w_j) + gamma*(dG(y).d + 2t G(d))
 //            is piecewise linear and nondecreasing: each round evaluates it
 //            at 16 points (FP32 per voxel, compensated FP32 across warps and
@@ -43,6 +56,12 @@
 #define LS_ROUNDS 4
 // per-CTA partial row: [N slots | 2 x 32 line-search values | cost | spare]
 #define PART_EXTRA 72
+// Step rule of the gradient projection (the oracle uses the same rule):
+// ABBmin with a memory of ABB_M short steps and switch ratio ABB_TAU for the
+// first ABB_ITERS iterations of a solve, the short step BB2 after them.
+#define ABB_M 3
+#define ABB_TAU 0.5
+#define ABB_ITERS 300
 #define LS_OFF(N, parity) ((N) + 32 * (parity))
 #define COST_OFF(N) ((N) + 64)
 
@@ -133,6 +152,24 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float x) {
   s = t;
 }
 
+// F'(z) of Eq. 1 from the excess e = z - T of a voxel over its threshold
+__device__ __forceinline__ float dF_e(float e, float al, float be) {
+  return e > 0.f ? 2.f * be * e : (e < 0.f ? 2.f * al * e : 0.f);
+}
+
+// s + c += a * (bh + bl), compensated: the rounding error of a*bh comes
+// exactly from an FMA, that of the sum from TwoSum (Knuth), and a*bl (bh + bl
+// a float pair) goes to the correction term
+__device__ __forceinline__ void dot2_add(float &s, float &c, float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  const float pe = __fmaf_rn(a, bh, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fmaf_rn(a, bl, __fadd_rn(e, pe)));
+}
+
 // derivative of the smoothing term G (Eq. 2) at beam k, from inverse gaps
 __device__ __forceinline__ double dG_inv(const double *y, const double *igl, const double *igr,
                                          int N, int k) {
@@ -199,8 +236,8 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     const float wq = w[q];
     if (wq == 0.f) continue;
     const int id = sid_of(sid, q);
-    const float T = s_tab[id], al = s_tab[256 + id], be = s_tab[512 + id];
-    const float e0 = z[q] - T;
+    const float al = s_tab[256 + id], be = s_tab[512 + id];
+    const float e0 = z[q];
     const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
     const float c0 = e0 > 0.f ? be : (e0 < 0.f ? al : cw);
     lin = fmaf(2.f * c0 * wq, wq, lin);
@@ -347,6 +384,42 @@ __device__ bool chol_packed_aug(float *A, int n, float *cb, float *dg) {
   return true;
 }
 
+// e = M y - T for the thread's VPT voxels (4 per subtile, subtile m at
+// off0 + m * mstride), compensated: starting from -T, every product of a
+// column entry with y (a float pair) enters through dot2_add.  Near the
+// solution many voxels sit close to their thresholds; there e is small and
+// this keeps it exact to a few units of its own last place, where plain FP32
+// sums of z would carry errors of the size of T's.
+template <int VPT>
+__device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z,
+                                              const uint32_t (&my_sid)[VPT / 4], const float *s_tab, const int *s_nz, const int *s_mask,
+                                              const float *s_yf, const float *s_ylo, int nnzs,
+                                              size_t off0, size_t mstride) {
+  constexpr int NG = VPT / 4;
+  float zc[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    z[v] = -s_tab[sid_of(my_sid, v)];
+    zc[v] = 0.f;
+  }
+  for (int q = 0; q < nnzs; ++q) {
+    const int s = s_nz[q], mk = s_mask[s];
+    const float *Ms = a.M + (size_t)s * a.Vpad + off0;
+    const float ys = s_yf[s], yl = s_ylo[s];
+#pragma unroll
+    for (int m = 0; m < NG; ++m) {
+      if (!(mk >> m & 1)) continue;
+      const float4 c = __ldg((const float4 *)(Ms + m * mstride) + threadIdx.x);
+      dot2_add(z[4 * m], zc[4 * m], c.x, ys, yl);
+      dot2_add(z[4 * m + 1], zc[4 * m + 1], c.y, ys, yl);
+      dot2_add(z[4 * m + 2], zc[4 * m + 2], c.z, ys, yl);
+      dot2_add(z[4 * m + 3], zc[4 * m + 3], c.w, ys, yl);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) z[v] = __fadd_rn(z[v], zc[v]);
+}
+
 template <int VPT, bool NEWTON>
 __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -372,7 +445,8 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   const int Np = (N + 1) & ~1;                    // keeps the float region below 16-byte aligned
   float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [Np] per slot
   float *s_df = s_yf + Np;                        // [Np] per slot
-  float *s_tab = s_df + Np;                       // [768]
+  float *s_ylo = s_df + Np;                       // [Np4] low part of y
+  float *s_tab = s_ylo + ((Np + 3) & ~3);         // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
   float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
   // s_fp is 16-byte aligned for its float4 accesses: the doubles above take a
@@ -449,7 +523,11 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     }
   }
   __syncthreads();
-  for (int s = tid; s < ns; s += nthr) s_yf[s] = (float)s_y[s_beam[s]];
+  for (int s = tid; s < ns; s += nthr) {
+    const double yk = s_y[s_beam[s]];
+    s_yf[s] = (float)yk;
+    s_ylo[s] = (float)(yk - (double)(float)yk);
+  }
   const int nnzs = s_i[1], npairs = s_i[2];
 
   uint32_t my_sid[NG];
@@ -458,27 +536,14 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   float z[VPT], w[VPT];
   __syncthreads();
 
-  // z = M y
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) z[v] = 0.f;
-#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
-  for (int q = 0; q < nnzs; ++q) {
-    const int s = s_nz[q], mk = s_mask[s];
-    const float *Ms = a.M + (size_t)s * a.Vpad;
-    const float ys = s_yf[s];
-#pragma unroll
-    for (int m = 0; m < NG; ++m) {
-      if (!(mk >> m & 1)) continue;
-      const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
-      z[4 * m] = fmaf(q.x, ys, z[4 * m]);
-      z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
-      z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
-      z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]);
-    }
-  }
+  // the dose excess e = M y - T of the thread's voxels
+  excess_from_y<VPT>(a, z, my_sid, s_tab, s_nz, s_mask, s_yf, s_ylo, nnzs, SUB_OFF(0), G * ST);
 
   int it = 0, status = VMAT_ENOTCONV, nsync = 0;
   double rho = 0.0, rho0 = 0.0, tol = 0.0;
+  double bb2_hist[ABB_M - 1];  // the last short steps, newest first (same in every thread)
+#pragma unroll
+  for (int q = 0; q < ABB_M - 1; ++q) bb2_hist[q] = INFINITY;
   bool alive = true;
   int ls_parity = 0;
   // phase clocks of CTA 0, kept in shared memory (one thread uses them)
@@ -494,13 +559,13 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     for (int m = 0; m < NG; ++m) {
       float4 f;
       int id = sid_of(my_sid, 4 * m);
-      f.x = vmat_dF(z[4 * m], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      f.x = dF_e(z[4 * m], s_tab[256 + id], s_tab[512 + id]);
       id = sid_of(my_sid, 4 * m + 1);
-      f.y = vmat_dF(z[4 * m + 1], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      f.y = dF_e(z[4 * m + 1], s_tab[256 + id], s_tab[512 + id]);
       id = sid_of(my_sid, 4 * m + 2);
-      f.z = vmat_dF(z[4 * m + 2], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      f.z = dF_e(z[4 * m + 2], s_tab[256 + id], s_tab[512 + id]);
       id = sid_of(my_sid, 4 * m + 3);
-      f.w = vmat_dF(z[4 * m + 3], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
+      f.w = dF_e(z[4 * m + 3], s_tab[256 + id], s_tab[512 + id]);
       *(float4 *)(s_fp + m * ST + 4 * tid) = f;
     }
     __syncthreads();
@@ -508,18 +573,23 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       const int s = s_pair[q] >> 3, m = s_pair[q] & 7;
       const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + SUB_OFF(m));
       const float4 *F4 = (const float4 *)(s_fp + m * ST);
-      float acc = 0.f;
+      float acc = 0.f, accc = 0.f;
 #pragma unroll 8
       for (int i = 0; i < lane4; ++i) {
         const float4 q = __ldg(Ms + lane + 32 * i);
         const float4 f = F4[lane + 32 * i];
-        acc = fmaf(q.x, f.x, acc);
-        acc = fmaf(q.y, f.y, acc);
-        acc = fmaf(q.z, f.z, acc);
-        acc = fmaf(q.w, f.w, acc);
+        dot2_add(acc, accc, q.x, f.x, 0.f);
+        dot2_add(acc, accc, q.y, f.y, 0.f);
+        dot2_add(acc, accc, q.z, f.z, 0.f);
+        dot2_add(acc, accc, q.w, f.w, 0.f);
       }
-      acc = warp_sumf(acc);
-      if (lane == 0) s_pp[q] = acc;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, acc, o), c2 = __shfl_xor_sync(0xffffffffu, accc, o);
+        comp_add(acc, accc, s2);
+        accc = __fadd_rn(accc, c2);
+      }
+      if (lane == 0) s_pp[q] = __fadd_rn(acc, accc);
     }
     __syncthreads();
     const int fstride = (N + 3) & ~3;
@@ -585,7 +655,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       const unsigned FULL = 0xffffffffu;
       const unsigned long long ABS = 0x7fffffffffffffffull;
       unsigned long long rb = 0, yb = 0, gb = 0;
-      float dyg = 0.f, dgg = 0.f;
+      float dyg = 0.f, dgg = 0.f, dyy = 0.f;
       for (int s = tid; s < ns; s += nthr) {
         const int k = s_beam[s];
         const double gk = s_g[s] + a.gamma * dG_inv(s_y, s_igl, s_igr, N, k);
@@ -599,6 +669,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         const float dgk = (float)(gk - s_gold[s]), dyk = (float)s_dy[s];
         dyg = fmaf(dyk, dgk, dyg);
         dgg = fmaf(dgk, dgk, dgg);
+        dyy = fmaf(dyk, dyk, dyy);
       }
       for (int o = 16; o; o >>= 1) {
         rb = max(rb, __shfl_xor_sync(FULL, rb, o));
@@ -606,25 +677,28 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         gb = max(gb, __shfl_xor_sync(FULL, gb, o));
         dyg += __shfl_xor_sync(FULL, dyg, o);
         dgg += __shfl_xor_sync(FULL, dgg, o);
+        dyy += __shfl_xor_sync(FULL, dyy, o);
       }
       unsigned long long *s_ru = (unsigned long long *)(s_res + 32);  // [3][16]
-      float *s_rf = (float *)(s_res + 32 + 48);                       // [2][16]
+      float *s_rf = (float *)(s_res + 32 + 48);                       // [3][16]
       if (lane == 0) {
         s_ru[warp] = rb;
         s_ru[16 + warp] = yb;
         s_ru[32 + warp] = gb;
         s_rf[warp] = dyg;
         s_rf[16 + warp] = dgg;
+        s_rf[32 + warp] = dyy;
       }
       __syncthreads();
       rb = yb = gb = 0;
-      dyg = dgg = 0.f;
+      dyg = dgg = dyy = 0.f;
       for (int q = 0; q < nwarp; ++q) {
         rb = max(rb, s_ru[q]);
         yb = max(yb, s_ru[16 + q]);
         gb = max(gb, s_ru[32 + q]);
         dyg += s_rf[q];
         dgg += s_rf[16 + q];
+        dyy += s_rf[32 + q];
       }
       rho = __longlong_as_double((long long)rb);
       if (it == 0) {
@@ -638,8 +712,22 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       if (it == 0)
         step = fmax(__longlong_as_double((long long)yb), 1.0) /
                fmax(__longlong_as_double((long long)gb), 1e-300);
-      else
-        step = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
+      else {
+        // adaptive Barzilai-Borwein (ABBmin): where the two BB steps differ by
+        // more than the factor ABB_TAU the least of the last ABB_M short (BB2)
+        // steps, else the long (BB1) step; BB2 alone once a solve has taken
+        // ABB_ITERS iterations (the rare solves where the adaptive rule
+        // stalls then finish at BB2's pace)
+        const double bb2 = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
+        const double bb1 = dyg > 0.f ? (double)(dyy / dyg) : 1e12;
+        double hmin = bb2;
+#pragma unroll
+        for (int q = 0; q < ABB_M - 1; ++q) hmin = fmin(hmin, bb2_hist[q]);
+#pragma unroll
+        for (int q = ABB_M - 2; q > 0; --q) bb2_hist[q] = bb2_hist[q - 1];
+        bb2_hist[0] = bb2;
+        step = it >= ABB_ITERS ? bb2 : (bb2 < ABB_TAU * bb1 ? hmin : bb1);
+      }
       step = fmin(fmax(step, 1e-12), 1e12);
       bool newton_ok = false;
       if (NEWTON) {
@@ -666,7 +754,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int v = 4 * m + q, id = sid_of(my_sid, v);
-            const float e = z[v] - s_tab[id];
+            const float e = z[v];
             s_sq[m * ST + 4 * tid + q] = sqrtf(2.f * (e > 0.f ? s_tab[512 + id] : s_tab[256 + id]));
           }
         __syncthreads();
@@ -929,7 +1017,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     // z itself is carried by the updates z += t w; every 16th iteration it is
     // recomputed from y so that FP32 rounding cannot accumulate
     {
-      const bool refresh = (it & 15) == 0;
+      const bool refresh = (it & 15) == 15;  // (iteration 0 starts from a fresh e)
       constexpr int STG = master_pipe_stages(VPT);
       float4 *pipe = (float4 *)s_rows;  // [STG][nthr], slot k of thread t at k*nthr + t
 #pragma unroll
@@ -944,20 +1032,26 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           cp_async_commit();
         }
         if (refresh) {
+          float4 zc4 = zz;
+          zz.x = -s_tab[sid_of(my_sid, 4 * m)];
+          zz.y = -s_tab[sid_of(my_sid, 4 * m + 1)];
+          zz.z = -s_tab[sid_of(my_sid, 4 * m + 2)];
+          zz.w = -s_tab[sid_of(my_sid, 4 * m + 3)];
           for (int q = 0; q < nm; ++q) {
             cp_async_wait<STG - 1>();
             const int slot = q & (STG - 1);
             const float4 v = pipe[slot * nthr + tid];
             const int sl = cl[q];
-            const float ys = s_yf[sl], ds = s_df[sl];
-            zz.x = fmaf(v.x, ys, zz.x); ww.x = fmaf(v.x, ds, ww.x);
-            zz.y = fmaf(v.y, ys, zz.y); ww.y = fmaf(v.y, ds, ww.y);
-            zz.z = fmaf(v.z, ys, zz.z); ww.z = fmaf(v.z, ds, ww.z);
-            zz.w = fmaf(v.w, ys, zz.w); ww.w = fmaf(v.w, ds, ww.w);
+            const float ys = s_yf[sl], yl = s_ylo[sl], ds = s_df[sl];
+            dot2_add(zz.x, zc4.x, v.x, ys, yl); ww.x = fmaf(v.x, ds, ww.x);
+            dot2_add(zz.y, zc4.y, v.y, ys, yl); ww.y = fmaf(v.y, ds, ww.y);
+            dot2_add(zz.z, zc4.z, v.z, ys, yl); ww.z = fmaf(v.z, ds, ww.z);
+            dot2_add(zz.w, zc4.w, v.w, ys, yl); ww.w = fmaf(v.w, ds, ww.w);
             if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
             cp_async_commit();
           }
-          z[4 * m] = zz.x; z[4 * m + 1] = zz.y; z[4 * m + 2] = zz.z; z[4 * m + 3] = zz.w;
+          z[4 * m] = __fadd_rn(zz.x, zc4.x); z[4 * m + 1] = __fadd_rn(zz.y, zc4.y);
+          z[4 * m + 2] = __fadd_rn(zz.z, zc4.z); z[4 * m + 3] = __fadd_rn(zz.w, zc4.w);
         } else {
           for (int q = 0; q < nm; ++q) {
             cp_async_wait<STG - 1>();
@@ -1100,6 +1194,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       s_dy[s] = dy;
       s_y[k] = NEWTON ? fmax(s_y[k] + dy, 0.0) : s_y[k] + dy;  // ratio test in FP64: clamp -0
       s_yf[s] = (float)s_y[k];
+      s_ylo[s] = (float)(s_y[k] - (double)s_yf[s]);
     }
     const float tf = (float)t;
 #pragma unroll
@@ -1116,25 +1211,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     return;
   }
 
-  // ---------------- final dose, derivative and cost at the solution
+  // ---------------- final dose, derivative and cost at the solution, from
+  // the carried excess (recomputed from y at the start and every 16th
+  // iteration, updated exactly along every step): z = e + T
   __syncthreads();
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) z[v] = 0.f;
-#pragma unroll(NG >= 6 ? 1 : NG >= 3 ? 2 : 4)
-  for (int q = 0; q < nnzs; ++q) {
-    const int s = s_nz[q], mk = s_mask[s];
-    const float *Ms = a.M + (size_t)s * a.Vpad;
-    const float ys = s_yf[s];
-#pragma unroll
-    for (int m = 0; m < NG; ++m) {
-      if (!(mk >> m & 1)) continue;
-      const float4 q = __ldg((const float4 *)(Ms + SUB_OFF(m)) + tid);
-      z[4 * m] = fmaf(q.x, ys, z[4 * m]);
-      z[4 * m + 1] = fmaf(q.y, ys, z[4 * m + 1]);
-      z[4 * m + 2] = fmaf(q.z, ys, z[4 * m + 2]);
-      z[4 * m + 3] = fmaf(q.w, ys, z[4 * m + 3]);
-    }
-  }
   double cst = 0.0;
 #pragma unroll
   for (int m = 0; m < NG; ++m) {
@@ -1142,9 +1222,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int v = 4 * m + q, id = sid_of(my_sid, v);
-      fo[q] = vmat_dF(z[v], s_tab[id], s_tab[256 + id], s_tab[512 + id]);
-      zo[q] = z[v];
-      cst += vmat_F((double)z[v], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
+      fo[q] = dF_e(z[v], s_tab[256 + id], s_tab[512 + id]);
+      zo[q] = __fadd_rn(z[v], s_tab[id]);
+      // cost against the FP64 threshold: z = e + T in the FP32 threshold, exactly
+      cst += vmat_F((double)z[v] + (double)s_tab[id], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
     }
     const size_t off = SUB_OFF(m) + 4 * tid;
     *(float4 *)(a.z_out + off) = make_float4(zo[0], zo[1], zo[2], zo[3]);
@@ -1200,7 +1281,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
   const size_t ng = vpt / 4;
   size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
-             (size_t)(2 * ((N + 1) & ~1) + 768 + LS_POINTS + 16 * 32) * 4 +  // yf df tab t ls
+             (size_t)(2 * ((N + 1) & ~1) + ((((N + 1) & ~1) + 3) & ~3) + 768 + LS_POINTS + 16 * 32) * 4 +
              (size_t)nthr * vpt * 4 +                          // F' tile
              (size_t)master_rows_len(N, nthr, vpt, newton) * 4 +  // line-search rows, pipeline, Newton
              (size_t)N * ng * 4 +                              // pair partials
