@@ -170,6 +170,17 @@ __device__ __forceinline__ void dot2_add(float &s, float &c, float a, float bh, 
   c = __fadd_rn(c, __fmaf_rn(a, bl, __fadd_rn(e, pe)));
 }
 
+// s + c += a * b, compensated as dot2_add (b without a low part)
+__device__ __forceinline__ void dot2_add1(float &s, float &c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
 // derivative of the smoothing term G (Eq. 2) at beam k, from inverse gaps
 __device__ __forceinline__ double dG_inv(const double *y, const double *igl, const double *igr,
                                          int N, int k) {
@@ -578,10 +589,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       for (int i = 0; i < lane4; ++i) {
         const float4 q = __ldg(Ms + lane + 32 * i);
         const float4 f = F4[lane + 32 * i];
-        dot2_add(acc, accc, q.x, f.x, 0.f);
-        dot2_add(acc, accc, q.y, f.y, 0.f);
-        dot2_add(acc, accc, q.z, f.z, 0.f);
-        dot2_add(acc, accc, q.w, f.w, 0.f);
+        dot2_add1(acc, accc, q.x, f.x);
+        dot2_add1(acc, accc, q.y, f.y);
+        dot2_add1(acc, accc, q.z, f.z);
+        dot2_add1(acc, accc, q.w, f.w);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
@@ -1014,8 +1025,8 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     // per own subtile, the thread streams its 16 bytes of each nonzero column
     // through a private ring of shared-memory slots (STG copies in flight;
     // the columns are mostly L2-resident, so latency bounds this pass)
-    // z itself is carried by the updates z += t w; every 16th iteration it is
-    // recomputed from y so that FP32 rounding cannot accumulate
+    // the excess e is carried by the updates e += t w; every 16th iteration it
+    // is recomputed from y so that FP32 rounding cannot accumulate
     {
       const bool refresh = (it & 15) == 15;  // (iteration 0 starts from a fresh e)
       constexpr int STG = master_pipe_stages(VPT);
