@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
-# current kernel (bench.py --case master: 8.086607 GB read + 5.964 MB written
+# current kernel (bench.py --case master: 8.083971 GB read + 6.172 MB written
 # for (2*30+1) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
 # to None whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (8.086607e9 + 5.964032e6) / ((2 * 30 + 1) * 150 * 221440 * 4 + 8 * 221440)
+MASTER_TRAFFIC_RATIO = (8.083971e9 + 6.172160e6) / ((2 * 30 + 1) * 150 * 221440 * 4 + 8 * 221440)
 UNIT = "CG iters/s"
 
 

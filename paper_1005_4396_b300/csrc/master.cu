@@ -1028,7 +1028,8 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     // the excess e is carried by the updates e += t w; every 16th iteration it
     // is recomputed from y so that FP32 rounding cannot accumulate
     {
-      const bool refresh = (it & 15) == 15;  // (iteration 0 starts from a fresh e)
+      const bool refresh = (it & 15) == 15;  // (iteration 0 starts from a fresh e; the update
+                                              // before a refresh forms y as a float pair)
       constexpr int STG = master_pipe_stages(VPT);
       float4 *pipe = (float4 *)s_rows;  // [STG][nthr], slot k of thread t at k*nthr + t
 #pragma unroll
@@ -1199,13 +1200,18 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     if (t <= 0.0) { status = VMAT_ENOTCONV; break; }
 
     // ---------------- update
+    // (y as a float pair is read only by the refresh of e in the next
+    // direction pass, so it is formed only before such an iteration)
+    const bool pair_next = ((it + 1) & 15) == 15;
     for (int s = tid; s < ns; s += nthr) {
       const int k = s_beam[s];
       const double dy = t * s_d[k];
       s_dy[s] = dy;
       s_y[k] = NEWTON ? fmax(s_y[k] + dy, 0.0) : s_y[k] + dy;  // ratio test in FP64: clamp -0
-      s_yf[s] = (float)s_y[k];
-      s_ylo[s] = (float)(s_y[k] - (double)s_yf[s]);
+      if (pair_next) {
+        s_yf[s] = (float)s_y[k];
+        s_ylo[s] = (float)(s_y[k] - (double)s_yf[s]);
+      }
     }
     const float tf = (float)t;
 #pragma unroll
