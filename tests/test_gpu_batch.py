@@ -66,3 +66,27 @@ def test_autotuner_and_fp16_dose_error(problems):
     finally:
         for p in plans:
             p.close()
+
+
+def test_batch_newton_matches_each_plan_alone(problems):
+    """The projected-Newton master under the batch's graph launch: each plan's
+    decisions, costs and intensities equal its own run with the same budget."""
+    plans = [vmat.Plan(p) for p in problems[:3]]
+    try:
+        for p in plans:
+            p.set_master_method("newton")
+        with vmat.Batch(plans) as batch:
+            batch.configure(2)
+            outs, _, _ = batch.run(kkt_tol=1e-6)
+            for plan, out in zip(plans, outs):
+                N = plan.cfg.n_angles
+                assert sorted(out["k"].tolist()) == list(range(N))
+                plan.reset()
+                solo = plan.colgen_run(kkt_tol=1e-6)
+                np.testing.assert_array_equal(solo["k"], out["k"])
+                np.testing.assert_array_equal(solo["cost"], out["cost"])
+                np.testing.assert_array_equal(solo["y"], out["y"])
+                assert np.all(out["iters"] <= 50)  # Newton: a few iterations per master
+    finally:
+        for p in plans:
+            p.close()
