@@ -66,6 +66,7 @@ def lib():
             "vo_line_search": (_c_d, [_c_i64, _p, _p, _p, _p, _p, _p, _c_d, _c_d, _c_d]),
             "vo_master": (_c_i32, [_c_i64, _c_i32, _p, _p, _c_i32, _p, _c_i32, _c_d, _p, _p, _p,
                                    _p, _c_d, _c_d, _c_i32, _p, _p, _p]),
+            "vo_dvh": (None, [_c_i64, _p, _p, _c_i32, _c_d, _c_i32, _p]),
             "vo_colgen": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32, _p, _p, _p, _p, _p, _p, _p,
                                    _p, _c_d, _c_i32, _c_i32, _c_i32, _c_d, _c_i32, _p, _p, _p,
                                    _c_i32, _c_i32] + [_p] * 12),
@@ -295,6 +296,22 @@ def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricin
         raise RuntimeError(f"oracle colgen failed: {rc}")
     rec.update(y=y, z=z, lleaf=lleaf, rleaf=rleaf)
     return rec
+
+
+# ---------------------------------------------------------------- plan evaluation (Fig. 2)
+def dvh(z, sid, n_struct, dose_max, n_bins) -> np.ndarray:
+    """Dose-volume histogram counts [n_struct, n_bins] of the dose z: voxel j
+    of structure sid[j] in bin b when b*w <= z_j < (b+1)*w, w =
+    dose_max/n_bins (doses >= dose_max in the last bin, < 0 in the first)."""
+    z = _f64(z)
+    sid = np.ascontiguousarray(sid, dtype=np.uint8)
+    if sid.size != z.size or (sid.size and int(sid.max()) >= n_struct):
+        raise ValueError("sid must give every voxel a structure < n_struct")
+    if not (dose_max > 0) or n_bins < 1:
+        raise ValueError("dose_max > 0 and n_bins >= 1 required")
+    out = np.zeros((n_struct, n_bins), np.int64)
+    lib().vo_dvh(z.size, _ptr(z), _ptr(sid), int(n_struct), float(dose_max), int(n_bins), _ptr(out))
+    return out
 
 
 # ---------------------------------------------------------------- dose-rate feasibility (Sec. 3)

@@ -30,8 +30,13 @@
  *     price; it is added even if that price is not negative.
  *   - Within a row: least value, then shortest interval, then smallest l;
  *     across beams: least price, then lowest index.
- *   - Master problem: projected gradient with the second Barzilai-Borwein
- *     step, an exact line search on [0,1] and the natural KKT residual.
+ *   - Master problem: projected gradient with the adaptive Barzilai-Borwein
+ *     step (ABBmin for a solve's first iterations, the short step after
+ *     them; see vo_master), an exact line search on [0,1] and the natural
+ *     KKT residual.
+ *   - Dose-volume histograms (the evaluation behind Fig. 2): bins of width
+ *     dose_max / n_bins from 0; the last bin also holds doses at or above
+ *     dose_max, the first one doses below 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -617,4 +622,23 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
   free(M); free(col_beam); free(occ); free(mask); free(fp); free(g); free(lk); free(rk);
   free(off);
   return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dose-volume histograms (plan evaluation, Fig. 2)                           */
+/* ------------------------------------------------------------------------ */
+/* counts[s*n_bins + b] = number of voxels j of structure s = sid[j] whose
+ * dose lies in bin b, i.e. b*w <= z_j < (b+1)*w with w = dose_max/n_bins;
+ * z_j >= dose_max goes to the last bin and z_j < 0 to the first.  The bin is
+ * found by comparing z_j with the edges b*dose_max/n_bins (each edge one
+ * FP64 product and quotient), scanning up from bin 0: plain and slow, and
+ * independent of how a kernel rounds z_j * n_bins / dose_max. */
+void vo_dvh(int64_t V, const double *z, const uint8_t *sid, int n_struct, double dose_max,
+            int n_bins, int64_t *counts) {
+  for (int64_t q = 0; q < (int64_t)n_struct * n_bins; ++q) counts[q] = 0;
+  for (int64_t j = 0; j < V; ++j) {
+    int b = 0;
+    while (b + 1 < n_bins && z[j] >= (double)(b + 1) * dose_max / (double)n_bins) ++b;
+    counts[(int64_t)sid[j] * n_bins + b] += 1;
+  }
 }

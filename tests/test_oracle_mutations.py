@@ -25,6 +25,10 @@ MUTATIONS = {
     "line search wrong curvature": ("Bc += 2.0 * c * wj * wj;", "Bc += c * wj * wj;"),
     "master ignores smoothing in gradient": ("grad[k] *= gamma;", "grad[k] *= 0.0;"),
     "aperture dose includes right leaf": ("for (int c = l[rr]; c < r[rr]; ++c) {", "for (int c = l[rr]; c <= r[rr] && c < C; ++c) {"),
+    "histogram edge goes down": ("z[j] >= (double)(b + 1) * dose_max", "z[j] > (double)(b + 1) * dose_max",
+                                 "test_oracle_dvh.py"),
+    "histogram drops the last bin": ("while (b + 1 < n_bins &&", "while (b + 2 < n_bins &&",
+                                     "test_oracle_dvh.py"),
     "smoothing price offset sign": ("for (int q = 0; q < N; ++q) off[q] *= gamma;",
                                     "for (int q = 0; q < N; ++q) off[q] *= -gamma;",
                                     "test_oracle_price_smoothing.py"),
