@@ -196,13 +196,21 @@ typedef struct {              /* caller-allocated host arrays (any may be NULL) 
                                  written only while profiling is on */
   int32_t *col_subtiles;      /* [n_iters] subtiles holding a nonzero of each added column
                                  (the master kernel streams only those) */
+  int32_t *priced_angle;      /* [n_iters] beam the pricing chose at each iteration; equals
+                                 angle_order except in replay, where the forced aperture is
+                                 added instead and this records the library's own choice on
+                                 the replayed state */
+  int16_t *priced_l, *priced_r; /* [n_iters*R] leaves of that choice, iteration-major */
 } vmat_colgen_result;
 
 /* Column generation (Sec. 2.2, Fig. 1) from the context's current plan:
  * n_iters times {prices of the free beams from F'(z); pricing; add column;
  * master problem}.  The master problems stop at kkt_tol relative to
  * max(rho_start, rho of the plan's first master problem).  The whole loop
- * runs on the device; the host reads the records once at the end.
+ * runs on the device; the host reads the records once at the end.  With
+ * forced_angle set (replay) iteration t adds the forced aperture, while
+ * price/runner_up/priced_* still record what the pricing itself chose on
+ * that state (decision-by-decision comparison with another solver's plan).
  * VMAT_ENOTCONV if some master problem hit its limit (records still
  * written). */
 VMAT_API vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *opts,
@@ -242,6 +250,16 @@ VMAT_API vmat_status vmat_aperture_adjoint_batch32(vmat_ctx *ctx, const int16_t 
                                                    const int16_t *r_dev, const float *GX_dev,
                                                    const float *Y_dev, const float *w_dev,
                                                    float *GY_dev);
+/* The differentiable forward in aperture intensities (Eq. 3) for 32
+ * intensity vectors on fixed apertures: X = A Y (as
+ * vmat_aperture_fluence_batch32; X_dev [B][32] float, written), Z = D^T X
+ * (Z_dev [n_vox][32] float), F'(Z) (fprime_dev [n_vox][32] float, or NULL)
+ * and cost_host [32] = sum_j F(Z[j][b]) + gamma * G(Y[:, b]), both parts
+ * reduced in FP64 (Eq. 1 and Eq. 2, ring if the context is cyclic). */
+VMAT_API vmat_status vmat_aperture_dose_cost_batch32(vmat_ctx *ctx, const int16_t *l_dev,
+                                                     const int16_t *r_dev, const float *Y_dev,
+                                                     float *X_dev, float *Z_dev, float *fprime_dev,
+                                                     double *cost_host);
 /* Smoothing term of Eq. 2 (ring if the context is cyclic) for 32 intensity
  * vectors: G_host [32] (FP64) and, if dG_dev is not NULL, dG/dY [N][32]. */
 VMAT_API vmat_status vmat_smoothing_batch32(vmat_ctx *ctx, const float *Y_dev, double *G_host,
@@ -377,10 +395,12 @@ VMAT_API vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_ite
  * over its n_vox voxels (row_ptr_dev [n_vox+1] int64, beamlet_dev [nnz]
  * int32 beamlet of each entry, val_dev [nnz] float D_ij), the fluence x_dev
  * [B] float, struct_id_dev [n_vox] uint8 (< n_struct) and params_dev
- * [3*n_struct] double (all T, then all alpha, then all beta of Eq. 1), and
- * gets z_dev [n_vox] float and fprime_dev [n_vox] float F'(z) (either may be
- * NULL) and cost_dev [1] double = sum_j F(z_j) reduced in FP64 in a fixed
- * order.  Everything is enqueued on cuda_stream (a cudaStream_t, NULL: legacy
+ * [3*n_struct] double (the voxel cost's per-structure thresholds T, then its
+ * underdose weights alpha, then its overdose weights beta), and gets z_dev
+ * [n_vox] float and fprime_dev [n_vox] float F'(z) (either may be NULL) and
+ * cost_dev [1] double = sum_j F(z_j) reduced in FP64 in a fixed order.  A
+ * voxel whose structure id is >= n_struct gets F' = NaN and makes the cost
+ * NaN (its parameters are not read).  Everything is enqueued on cuda_stream (a cudaStream_t, NULL: legacy
  * default stream) and the call returns without waiting.
  * Its only scratch, one FP64 partial cost per 8 voxels, is a file-scope
  * __device__ array of 65,536 doubles (512 KiB) that every GPU loading the
@@ -389,8 +409,10 @@ VMAT_API vmat_status vmat_batch_colgen_run(vmat_batch *b, int32_t master_max_ite
  * contents, so calls that may overlap on the GPU (different streams, or
  * different threads) race and must be serialised by the caller.  The first
  * call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Errors are
- * reported by vmat_last_error(NULL). */
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point on a device
+ * after cudaDeviceReset of that device (the kept address belongs to the old
+ * context).  Errors are reported by vmat_last_error(NULL). */
 VMAT_API vmat_status vmat_dose_cost_noalloc(int32_t n_vox, const int64_t *row_ptr_dev,
                                             const int32_t *beamlet_dev, const float *val_dev,
                                             const float *x_dev, const uint8_t *struct_id_dev,

@@ -13,7 +13,6 @@ A is the aperture map of the leaves l, r [N*R] (int16, on the device).
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import vmat
@@ -40,12 +39,12 @@ class _ApertureDoseCost(torch.autograd.Function):
     def forward(ctx, Y, plan, l, r):
         Y = Y.contiguous()
         X = torch.empty(plan.cfg.n_beamlets, 32, dtype=torch.float32, device=Y.device)
-        vmat.vmat_aperture_fluence_batch32(plan.ctx, l, r, Y, X)
-        Z, Fp, cost = plan.dose_batch32(X)
-        Gs = vmat.vmat_smoothing_batch32(plan.ctx, Y)
+        Z = torch.empty(plan.prob.n_vox, 32, dtype=torch.float32, device=Y.device)
+        Fp = torch.empty_like(Z)
+        cost = vmat.vmat_aperture_dose_cost_batch32(plan.ctx, l, r, Y, X, Z, Fp)
         ctx.plan = plan
         ctx.save_for_backward(Fp, Y, l, r)
-        return torch.as_tensor(cost + plan.cfg.gamma * Gs, dtype=torch.float64, device=Y.device)
+        return torch.as_tensor(cost, dtype=torch.float64, device=Y.device)
 
     @staticmethod
     def backward(ctx, gcost):

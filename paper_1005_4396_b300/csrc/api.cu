@@ -260,7 +260,9 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   cudaStream_t st = ctx->stream;
   // device records (one block) and forced plan
   size_t nn = n > 0 ? n : 1;
-  size_t bytes = nn * (4 * 4 + 4 * 8) + 64 + (o->forced_angle ? nn * (4 + 4 * (size_t)R) + 64 : 0);
+  const bool want_priced = res && (res->priced_l || res->priced_r);
+  size_t bytes = nn * (4 * 4 + 4 * 8) + 64 + (o->forced_angle ? nn * (4 + 4 * (size_t)R) + 64 : 0) +
+                 (want_priced ? nn * 4 * (size_t)R + 64 : 0);
   char *blk = nullptr;
   VMAT_CUDA(ctx, cudaMallocAsync((void **)&blk, bytes, st));
   Records rec;
@@ -274,8 +276,15 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   rec.tiles = rec.status + nn;
   int32_t *fk = nullptr;
   int16_t *fl = nullptr, *fr = nullptr;
+  int16_t *pl = nullptr, *pr = nullptr;  // leaves of the pricing result at every iteration
+  char *tail = (char *)(rec.tiles + nn);
+  if (want_priced) {
+    pl = (int16_t *)(((uintptr_t)tail + 15) & ~(uintptr_t)15);
+    pr = pl + nn * R;
+    tail = (char *)(pr + nn * R);
+  }
   if (o->forced_angle) {
-    fk = (int32_t *)(((uintptr_t)(rec.tiles + nn) + 15) & ~(uintptr_t)15);
+    fk = (int32_t *)(((uintptr_t)tail + 15) & ~(uintptr_t)15);
     fl = (int16_t *)(fk + nn);
     fr = fl + nn * R;
     cudaMemcpyAsync(fk, o->forced_angle, n * 4, cudaMemcpyHostToDevice, st);
@@ -302,6 +311,10 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
     mark(t, 1);
     s = vmat_launch_pricing_rec(ctx, ctx->g, rec.k + t, rec.p + t, rec.p2 + t);
     if (s != VMAT_OK) break;
+    if (pl) {  // the pricing's own leaves, before a forced aperture replaces them
+      cudaMemcpyAsync(pl + (size_t)t * R, ctx->sel_l, (size_t)R * 2, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(pr + (size_t)t * R, ctx->sel_r, (size_t)R * 2, cudaMemcpyDeviceToDevice, st);
+    }
     if (fk) {
       s = vmat_launch_force(ctx, fk, fl, fr, t);
       if (s != VMAT_OK) break;
@@ -315,9 +328,7 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
                            rec.cost + t, rec.rho + t, rec.iters + t, rec.status + t);
     mark(t, 4);
   }
-  if (fk) {  // the beam actually added at each step is the forced one
-    cudaMemcpyAsync(rec.k, fk, n * 4, cudaMemcpyDeviceToDevice, st);
-  }
+  // rec.k holds the pricing's choice; with forcing, the beam added is the forced one
   std::vector<int32_t> hk(nn), hit(nn), hst(nn), htl(nn);
   std::vector<double> hp(nn), hp2(nn), hc(nn), hr(nn);
   if (n > 0) {
@@ -329,6 +340,10 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
     cudaMemcpyAsync(hp2.data(), rec.p2, n * 8, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hc.data(), rec.cost, n * 8, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hr.data(), rec.rho, n * 8, cudaMemcpyDeviceToHost, st);
+  }
+  if (n > 0 && pl) {
+    if (res->priced_l) cudaMemcpyAsync(res->priced_l, pl, (size_t)n * R * 2, cudaMemcpyDeviceToHost, st);
+    if (res->priced_r) cudaMemcpyAsync(res->priced_r, pr, (size_t)n * R * 2, cudaMemcpyDeviceToHost, st);
   }
   if (res && res->l) cudaMemcpyAsync(res->l, ctx->lleaf, (size_t)N * R * 2, cudaMemcpyDeviceToHost, st);
   if (res && res->r) cudaMemcpyAsync(res->r, ctx->rleaf, (size_t)N * R * 2, cudaMemcpyDeviceToHost, st);
@@ -349,7 +364,8 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   if (s2 != VMAT_OK) return s2;
   if (res) {
     for (int t = 0; t < n; ++t) {
-      if (res->angle_order) res->angle_order[t] = hk[t];
+      if (res->angle_order) res->angle_order[t] = o->forced_angle ? o->forced_angle[t] : hk[t];
+      if (res->priced_angle) res->priced_angle[t] = hk[t];
       if (res->price) res->price[t] = hp[t];
       if (res->runner_up) res->runner_up[t] = hp2[t];
       if (res->cost) res->cost[t] = hc[t];

@@ -136,3 +136,32 @@ extern "C" vmat_status vmat_smoothing_batch32(vmat_ctx *ctx, const float *Y_dev,
   VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return VMAT_OK;
 }
+
+// Eq. 3 for 32 intensity vectors on fixed apertures: X = A Y, Z = D^T X with
+// F'(Z), and cost_b = sum_j F(Z_jb) (FP64) + gamma * G(Y_b) (FP64, Eq. 2),
+// the two parts added here in FP64.
+extern "C" vmat_status vmat_aperture_dose_cost_batch32(vmat_ctx *ctx, const int16_t *l_dev,
+                                                       const int16_t *r_dev, const float *Y_dev,
+                                                       float *X_dev, float *Z_dev,
+                                                       float *fprime_dev, double *cost_host) {
+  if (!ctx || !Y_dev || !X_dev || !Z_dev || !cost_host)
+    return ctx ? vmat_fail(ctx, VMAT_EINVAL, "NULL argument") : VMAT_EINVAL;
+  vmat_status s = check_leaves(ctx, l_dev, r_dev);
+  if (s != VMAT_OK) return s;
+  const int64_t n = ctx->B * 32;
+  k_fluence32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(l_dev, r_dev, Y_dev, ctx->R,
+                                                                     ctx->C, ctx->B, X_dev);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
+  double *cdev = ctx->red + ctx->red_len - 64;  // [0, 32): voxel cost, [32, 64): G
+  s = vmat_launch_dose_batch32(ctx, X_dev, Z_dev, fprime_dev, cdev);
+  if (s != VMAT_OK) return s;
+  k_smooth32<<<1, 32, 0, ctx->stream>>>(Y_dev, ctx->theta, ctx->N, ctx->cyclic, cdev + 32, nullptr);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
+  double h[64];
+  VMAT_CUDA(ctx, cudaMemcpyAsync(h, cdev, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int b = 0; b < 32; ++b) cost_host[b] = h[b] + ctx->inactive_cost + ctx->gamma * h[32 + b];
+  return VMAT_OK;
+}

@@ -22,7 +22,10 @@ static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS];
 
 // Device address of the scratch array, looked up once per device (with that
 // device current) and cached; the host-side name of the array is only a
-// stand-in and must never be passed to a kernel.
+// stand-in and must never be passed to a kernel.  The cache lives as long as
+// the process: a cudaDeviceReset gives the device a new context in which the
+// cached address is no longer valid, so a process that resets a device must
+// not call this entry point on it afterwards.
 static std::mutex g_noalloc_mu;
 static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
@@ -61,10 +64,15 @@ __global__ void __launch_bounds__(256) k_dose_noalloc(
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       const int q = sid[j];
-      const double T = prm[q], al = prm[n_struct + q], be = prm[2 * n_struct + q];
       if (z) z[j] = acc;
-      if (fp) fp[j] = vmat_dF(acc, (float)T, (float)al, (float)be);
-      c = vmat_F((double)acc, T, al, be);
+      if (q < n_struct) {
+        const double T = prm[q], al = prm[n_struct + q], be = prm[2 * n_struct + q];
+        if (fp) fp[j] = vmat_dF(acc, (float)T, (float)al, (float)be);
+        c = vmat_F((double)acc, T, al, be);
+      } else {  // structure id beyond params: flag the voxel, read nothing
+        if (fp) fp[j] = __int_as_float(0x7fc00000);
+        c = __longlong_as_double(0x7ff8000000000000ll);
+      }
     }
   }
   if (lane == 0) s_cost[warp] = c;

@@ -65,7 +65,8 @@ class vmat_colgen_opts(ctypes.Structure):
 class vmat_colgen_result(ctypes.Structure):
     _fields_ = [("angle_order", _p), ("l", _p), ("r", _p), ("y", _p), ("price", _p),
                 ("runner_up", _p), ("cost", _p), ("kkt", _p), ("master_iters", _p),
-                ("phase_ms", _p), ("col_subtiles", _p)]
+                ("phase_ms", _p), ("col_subtiles", _p), ("priced_angle", _p), ("priced_l", _p),
+                ("priced_r", _p)]
 
 
 EXPORTS = {
@@ -89,6 +90,7 @@ EXPORTS = {
     "vmat_aperture_fluence_batch32": [_p, _p, _p, _p, _p],
     "vmat_aperture_adjoint_batch32": [_p, _p, _p, _p, _p, _p, _p],
     "vmat_smoothing_batch32": [_p, _p, _p, _p],
+    "vmat_aperture_dose_cost_batch32": [_p, _p, _p, _p, _p, _p, _p, _p],
     "vmat_set_master_budget": [_p, _i32],
     "vmat_batch_create": [_p, _i32, _p, ctypes.POINTER(_p)],
     "vmat_batch_destroy": [_p],
@@ -253,16 +255,19 @@ def vmat_colgen_run(ctx, N, R, n_iters, master_max_iters=100000, kkt_tol=1e-6, f
     out = dict(k=np.zeros(n, np.int32), lleaf=np.zeros(N * R, np.int16),
                rleaf=np.zeros(N * R, np.int16), y=np.zeros(N), p=np.zeros(n), p2=np.zeros(n),
                cost=np.zeros(n), rho=np.zeros(n), iters=np.zeros(n, np.int32),
-               phase_ms=np.zeros((n, 4)), col_subtiles=np.zeros(n, np.int32))
+               phase_ms=np.zeros((n, 4)), col_subtiles=np.zeros(n, np.int32),
+               priced_k=np.zeros(n, np.int32), priced_l=np.zeros((n, R), np.int16),
+               priced_r=np.zeros((n, R), np.int16))
     res = vmat_colgen_result(*[out[k].ctypes.data for k in
                                ("k", "lleaf", "rleaf", "y", "p", "p2", "cost", "rho", "iters",
-                                "phase_ms", "col_subtiles")])
+                                "phase_ms", "col_subtiles", "priced_k", "priced_l", "priced_r")])
     st = load_library().vmat_colgen_run(ctx, ctypes.byref(opts), ctypes.byref(res))
     out["status"] = st
     if st != VMAT_OK and not (allow_notconv and st == VMAT_ENOTCONV):
         _check(ctx, st)
     if n_iters == 0:
-        for k in ("k", "p", "p2", "cost", "rho", "iters", "phase_ms", "col_subtiles"):
+        for k in ("k", "p", "p2", "cost", "rho", "iters", "phase_ms", "col_subtiles", "priced_k",
+                  "priced_l", "priced_r"):
             out[k] = out[k][:0]
     return out
 
@@ -296,6 +301,15 @@ def vmat_aperture_fluence_batch32(ctx, l, r, Y, X):
 def vmat_aperture_adjoint_batch32(ctx, l, r, GX, GY, Y=None, w=None):
     _check(ctx, load_library().vmat_aperture_adjoint_batch32(ctx, _ptr(l), _ptr(r), _ptr(GX),
                                                              _ptr(Y), _ptr(w), _ptr(GY)))
+
+
+def vmat_aperture_dose_cost_batch32(ctx, l, r, Y, X, Z, fprime=None):
+    """Eq. 3 cost [32] (float64) of 32 intensity vectors Y [N, 32] on the
+    apertures l, r; fills X = A Y, Z = D^T X and F'(Z) (if given)."""
+    cost = np.zeros(32)
+    _check(ctx, load_library().vmat_aperture_dose_cost_batch32(ctx, _ptr(l), _ptr(r), _ptr(Y), _ptr(X),
+                                                               _ptr(Z), _ptr(fprime), cost.ctypes.data))
+    return cost
 
 
 def vmat_smoothing_batch32(ctx, Y, dG=None):
