@@ -152,6 +152,27 @@ def small_config(nx=20, ny=18, nz=6, n_angles=12, n_rows=6, n_cols=8, **kw) -> P
     return dataclasses.replace(c, **kw)
 
 
+def asym_config(nx=20, ny=18, nz=6, n_angles=12, n_rows=6, n_cols=8, **kw) -> PlanConfig:
+    """small_config with the target and the organ at risk moved off the
+    grid's symmetry planes, and D rounded to FP32-representable values.  On
+    the centred phantoms opposite beams see mirror images of one another and
+    their prices tie exactly; here no two beams or leaf intervals tie, so a
+    whole plan's decisions can be compared one by one."""
+    base = small_config(nx=nx, ny=ny, nz=nz, n_angles=n_angles, n_rows=n_rows, n_cols=n_cols)
+    h = base.h
+    c = dataclasses.replace(
+        base, name="asym", round_f32=True,
+        structures=[
+            Structure("target", "ellipsoid", (0.13 * nx * h, -0.07 * ny * h, 0.05 * nz * h,
+                                                 0.27 * nx * h, 0.22 * ny * h, 0.33 * nz * h),
+                      1.0, 1.0, 1.0),
+            Structure("oar", "ellipsoid", (-0.12 * nx * h, 0.27 * ny * h, -0.04 * nz * h,
+                                              0.14 * nx * h, 0.16 * ny * h, 0.38 * nz * h),
+                      0.5, 0.0, 0.5),
+        ])
+    return dataclasses.replace(c, **kw)
+
+
 CONFIGS = {"tiny": tiny_config, "prostate": prostate_config, "headneck": headneck_config}
 
 

@@ -1,11 +1,14 @@
-"""Many plans at once: the graph-launched batch reproduces each plan's own
-column generation exactly, the autotuner picks an SM share that works, and
-FP16-D plans stay within 0.5% of the prescription of the FP64 dose."""
+"""Many plans at once: every batched plan's decisions and costs against the
+FP64 oracle (tests/decisions.py), the graph-launched batch reproducing each
+plan's own column generation exactly, the autotuner picking an SM share that
+works, and FP16-D plans within 0.5% of the prescription of the FP64 dose."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1005_4396_b300 import inputs
+
+import decisions as dec
 
 pytestmark = pytest.mark.gpu
 
@@ -22,6 +25,35 @@ def problems():
     cfgs = [inputs.small_config(nx=20 + 3 * i, ny=18 + 2 * i, nz=6 + (i % 2), n_angles=12 + 6 * i,
                                 n_rows=6 + 2 * (i % 3), n_cols=8, seed=10 + i) for i in range(5)]
     return [inputs.make_problem(c) for c in cfgs]
+
+
+@pytest.fixture(scope="module")
+def asym_problems():
+    # four off-centre plans of uneven size whose decisions never tie
+    cfgs = [inputs.asym_config(nx=20 + 3 * i, ny=18 + 2 * i, nz=6 + (i % 2), n_angles=12 + 5 * i,
+                               n_rows=6 + (i % 3), n_cols=8 + (i % 2), cyclic=i != 2, seed=30 + i)
+            for i in range(4)]
+    return [inputs.make_problem(c) for c in cfgs]
+
+
+def test_batched_plans_vs_oracle(asym_problems):
+    """Each plan of a batch (side by side on disjoint SMs, one graph launch)
+    takes the oracle's decisions wherever they are not near-ties, with its
+    costs within 1e-5."""
+    refs = [dec.oracle_plan(p) for p in asym_problems]
+    plans = [vmat.Plan(p) for p in asym_problems]
+    try:
+        with vmat.Batch(plans) as batch:
+            batch.configure(2)
+            outs, _, _ = batch.run(kkt_tol=dec.GPU_KKT)
+        for prob, ref, out in zip(asym_problems, refs, outs):
+            n = prob.cfg.iterations
+            first_tie = next((t for t in range(n) if dec.margin(ref, t) <= dec.NEAR_TIE), n)
+            agree = dec.check_unforced(out, ref, prob.cfg.n_rows)
+            assert agree >= first_tie and agree >= n - 2, (prob.cfg.name, agree, first_tie, n)
+    finally:
+        for p in plans:
+            p.close()
 
 
 def test_batch_matches_each_plan_run_alone(problems):

@@ -12,11 +12,15 @@ its last master problem within FP32 reach of zero).
 Head-and-neck phantom (160x160x96 voxels, 180 beams, 60x40 MLC, 6.3e8
 nonzeros): FP32, FP16 and BF16 storage of D against the FP64 dose of a
 deliverable plan scaled to the prescription (Sec. 2.1, Eq. 1)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_1005_4396_b300 import inputs
+
+import decisions as dec
 
 pytestmark = pytest.mark.gpu
 
@@ -26,11 +30,6 @@ if not torch.cuda.is_available():
 
 from paper_1005_4396_b300 import vmat  # noqa: E402
 
-# Decisions are compared where both sides priced the same way: the GPU's masters
-# stop at relative KKT 1e-6 (its FP32 floor), the oracle's at 1e-8, so their
-# aperture prices differ by ~1e-6 relative and a decision whose margin lies
-# within 10x of that is a near-tie (pricing on identical prices is bit-exact).
-NEAR_TIE = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -130,33 +129,45 @@ def test_prostate_pricing_bit_exact_and_columns(prostate, pplan):
     pplan.reset()
 
 
-def _first_difference(gpu, ref, R, tol=NEAR_TIE):
-    for t in range(len(ref["k"])):
-        k = ref["k"][t]
-        same = gpu["k"][t] == k and np.array_equal(_leaves(gpu["lleaf"], k, R), _leaves(ref["lleaf"], k, R)) \
-            and np.array_equal(_leaves(gpu["rleaf"], k, R), _leaves(ref["rleaf"], k, R))
-        if not same:
-            assert min(ref["margin"][t], ref["row_margin"][t]) <= tol, f"iteration {t} differs off a tie"
-            return t
-    return len(ref["k"])
-
-
 def test_prostate_first_iterations(prostate, pplan):
+    """The prostate phantom is mirror-symmetric left to right: its first
+    decisions are near-ties between mirror beams (margins ~1e-8).  Unforced,
+    the plans agree up to the first of them; the oracle's first 20 decisions
+    replayed: every one that is not a near-tie identical, every price and
+    master cost within 1e-5."""
     cfg = prostate.cfg
-    R, n = cfg.n_rows, 6
-    ref = oracle.colgen(prostate, n_iter=n, eps=1e-8)
+    R, n = cfg.n_rows, 20
+    ref = dec.oracle_plan(prostate, n_iter=n)
     pplan.reset()
-    gpu = pplan.colgen_run(n_iters=n, kkt_tol=1e-6)
-    first = _first_difference(gpu, ref, R)
-    np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
-    # the oracle's decisions replayed on the GPU: every master cost within 1e-5
-    fl = np.array([_leaves(ref["lleaf"], k, R) for k in ref["k"]])
-    fr = np.array([_leaves(ref["rleaf"], k, R) for k in ref["k"]])
+    gpu = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT)
+    dec.check_unforced(gpu, ref, R)
     pplan.reset()
-    rep = pplan.colgen_run(n_iters=n, kkt_tol=1e-6, forced=(ref["k"], fl, fr))
-    np.testing.assert_array_equal(rep["k"], ref["k"])
-    np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
+    rep = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
+    dec.check_replay(rep, ref, R)
     pplan.reset()
+
+
+def test_prostate_off_centre_decisions():
+    """The prostate workload with its target moved 7 mm to the left, 2 mm
+    anterior and 4 mm up, which breaks the mirror symmetry: the oracle's
+    first 24 decisions replayed at full size (1.05M voxels, 288,000
+    beamlets), all that are not near-ties compared bit for bit."""
+    base = inputs.prostate_config()
+    st = list(base.structures)
+    st[0] = dataclasses.replace(st[0], params=(7.0, -2.0, 4.0, 30.0, 25.0, 30.0))
+    cfg = dataclasses.replace(base, structures=st)
+    prob = inputs.make_problem(cfg)
+    R, n = cfg.n_rows, 24
+    ref = dec.oracle_plan(prob, n_iter=n)
+    first_tie = next((t for t in range(n) if dec.margin(ref, t) <= dec.NEAR_TIE), n)
+    with vmat.Plan(prob, val_f32=True) as plan:
+        gpu = plan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT)
+        assert dec.check_unforced(gpu, ref, R) >= first_tie
+        plan.reset()
+        rep = plan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
+    compared, ties = dec.check_replay(rep, ref, R)
+    assert compared >= 12, (compared, ties)
+    print(f"off-centre prostate: {compared} of {n} decisions compared bit for bit, {ties} near-ties")
 
 
 def test_prostate_whole_plan(prostate, pplan):

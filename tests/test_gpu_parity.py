@@ -1,12 +1,16 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle on
 seeded inputs.  Tolerances: FP32 dose, price and cost within 1e-5 relative;
 pricing decisions bit-exact when both sides take them in FP32 on the same
-prices; reduced-precision D within 0.5% of the largest prescription."""
+prices; column-generation decisions bit-exact except at near-ties (margin
+<= 1e-6, tests/decisions.py); reduced-precision D within 0.5% of the
+largest prescription."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1005_4396_b300 import inputs
+
+import decisions as dec
 
 pytestmark = pytest.mark.gpu
 
@@ -15,13 +19,6 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 from paper_1005_4396_b300 import vmat  # noqa: E402
-
-# Decisions are compared where both sides priced the same way: the GPU's masters
-# stop at relative KKT 1e-6 (its FP32 floor), the oracle's at 1e-8, so their
-# aperture prices differ by ~1e-6 relative and a decision whose margin lies
-# within 10x of that is a near-tie (pricing on identical prices is bit-exact).
-NEAR_TIE = 1e-5
-
 
 @pytest.fixture(scope="module")
 def tiny():
@@ -176,7 +173,7 @@ def test_master_parity(tiny, tiny_plan):
     for k in order:
         tiny_plan.add_column(k, ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
     y = np.zeros(cfg.n_angles)
-    res = tiny_plan.master_step(max_iters=200000, kkt_tol=1e-7, y=y)
+    res = tiny_plan.master_step(max_iters=200000, kkt_tol=dec.GPU_KKT, y=y)
     assert res["status"] == vmat.VMAT_OK, res
     M = np.array([oracle.aperture_dose(tiny, k, ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
                   for k in order])
@@ -184,67 +181,57 @@ def test_master_parity(tiny, tiny_plan):
                         tiny.beta, cfg.gamma, cfg.cyclic, np.zeros(cfg.n_angles), eps=1e-11)
     assert ref["status"] == 0
     assert res["cost"] == pytest.approx(ref["cost"], rel=1e-5)
+    # converged to KKT 1e-9 against 1e-11: the dose within 1e-5 of its largest
+    # value; y only as far as the near-collinear columns of neighbouring beams
+    # determine it (the cost is flat along their differences)
     z = tiny_plan.plan_dose().cpu().numpy()
-    np.testing.assert_allclose(z, ref["z"], rtol=0, atol=2e-4 * ref["z"].max())
-    np.testing.assert_allclose(y, ref["y"], rtol=0, atol=5e-3 * ref["y"].max())
+    np.testing.assert_allclose(z, ref["z"], rtol=0, atol=1e-5 * ref["z"].max())
+    np.testing.assert_allclose(y, ref["y"], rtol=0, atol=1e-4 * ref["y"].max())
     assert np.all(y >= 0) and np.all(y[occ == 0] == 0)
     tiny_plan.reset()
 
 
 # ------------------------------------------------------------------ column generation
-def _compare_decisions(gpu, ref, R, tol=NEAR_TIE):
-    """Index of the first iteration whose beam or leaves differ, checking that
-    every difference sits on a near-tie (margin <= tol relative)."""
-    n = len(ref["k"])
-    for t in range(n):
-        k = ref["k"][t]
-        same = gpu["k"][t] == k
-        if same:
-            same = (np.array_equal(gpu["lleaf"][k * R:(k + 1) * R], ref["lleaf"][k * R:(k + 1) * R])
-                    and np.array_equal(gpu["rleaf"][k * R:(k + 1) * R], ref["rleaf"][k * R:(k + 1) * R]))
-        if not same:
-            assert min(ref["margin"][t], ref["row_margin"][t]) <= tol, (
-                f"iteration {t}: decisions differ without a near-tie "
-                f"(margin {ref['margin'][t]:.3e}, row margin {ref['row_margin'][t]:.3e})")
-            return t
-    return n
-
-
 def test_colgen_tiny_decisions_and_costs(tiny, tiny_plan):
+    """The tiny workload as specified (D in FP64 on the oracle's side, FP32
+    on the library's): decisions as in tests/decisions.py, the replayed
+    oracle plan, and the plan dose of the library's own plan."""
     cfg = tiny.cfg
     R = cfg.n_rows
-    ref = oracle.colgen(tiny, eps=1e-8)
+    ref = dec.oracle_plan(tiny)
     tiny_plan.reset()
-    gpu = tiny_plan.colgen_run(kkt_tol=1e-6)
-    first = _compare_decisions(gpu, ref, R)
-    # costs agree while the decisions agree
-    np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
-    # replay the oracle's plan on the GPU: every cost within 1e-5
-    fl = np.array([ref["lleaf"][k * R:(k + 1) * R] for k in ref["k"]])
-    fr = np.array([ref["rleaf"][k * R:(k + 1) * R] for k in ref["k"]])
-    tiny_plan.reset()
-    rep = tiny_plan.colgen_run(kkt_tol=1e-6, forced=(ref["k"], fl, fr))
-    np.testing.assert_array_equal(rep["k"], ref["k"])
-    np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
-    assert np.all(np.diff(rep["cost"]) <= 1e-6 * rep["cost"][:-1])
-    # the plan dose is the dose of the GPU's own plan (apertures, y) to 1e-5
+    gpu = tiny_plan.colgen_run(kkt_tol=dec.GPU_KKT)
+    first_tie = next(t for t in range(cfg.iterations) if dec.margin(ref, t) <= dec.NEAR_TIE)
+    assert dec.check_unforced(gpu, ref, R) >= first_tie
+    # the plan dose is the dose of the library's own plan (apertures, y) to 1e-5
     z = tiny_plan.plan_dose().cpu().numpy()
-    z_own = oracle.dose(tiny, oracle.aperture_fluence(cfg, rep["lleaf"], rep["rleaf"], rep["y"]))
+    z_own = oracle.dose(tiny, oracle.aperture_fluence(cfg, gpu["lleaf"], gpu["rleaf"], gpu["y"]))
     np.testing.assert_allclose(z, z_own, rtol=1e-5, atol=1e-6 * z_own.max())
-    # and differs from the oracle's plan dose only as far as the two master
-    # solves stop at different KKT tolerances (1e-6 vs 1e-8 relative)
-    np.testing.assert_allclose(z, ref["z"], rtol=0, atol=1e-3 * ref["z"].max())
+    # replay the oracle's plan: its decisions wherever they are not near-ties
+    tiny_plan.reset()
+    rep = tiny_plan.colgen_run(kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
+    compared, ties = dec.check_replay(rep, ref, R)
+    assert compared >= cfg.iterations - 3, (compared, ties)
+    assert np.all(np.diff(rep["cost"]) <= 1e-6 * rep["cost"][:-1])
+    # the same apertures and converged intensities: the oracle's plan dose
+    z = tiny_plan.plan_dose().cpu().numpy()
+    np.testing.assert_allclose(z, ref["z"], rtol=0, atol=1e-4 * ref["z"].max())
     tiny_plan.reset()
 
 
 def test_colgen_small_path_neighbours(small):
+    """The centred small phantom on a path of beams: mirror-image beams tie,
+    so decisions agree up to the first near-tie and the replay compares the
+    rest."""
     cfg = inputs.small_config(cyclic=False, max_leaf_step=2)
     prob = inputs.Problem(**{**small.__dict__, "cfg": cfg})
-    ref = oracle.colgen(prob, eps=1e-8)
+    ref = dec.oracle_plan(prob)
     with vmat.Plan(prob) as plan:
-        gpu = plan.colgen_run(kkt_tol=1e-6)
-    first = _compare_decisions(gpu, ref, cfg.n_rows)
-    np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
+        gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
+        dec.check_unforced(gpu, ref, cfg.n_rows)
+        plan.reset()
+        rep = plan.colgen_run(kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, cfg.n_rows))
+    dec.check_replay(rep, ref, cfg.n_rows)
 
 
 @pytest.mark.parametrize("method", ["pg", "newton"])
@@ -253,18 +240,14 @@ def test_colgen_odd_beam_count(small, method):
     master kernel; both master methods still match the oracle."""
     cfg = inputs.small_config(n_angles=13)
     prob = inputs.make_problem(cfg)
-    ref = oracle.colgen(prob, eps=1e-8)
+    ref = dec.oracle_plan(prob)
     with vmat.Plan(prob) as plan:
         plan.set_master_method(method)
-        gpu = plan.colgen_run(kkt_tol=1e-6)
-        first = _compare_decisions(gpu, ref, cfg.n_rows)
-        np.testing.assert_allclose(gpu["cost"][:first], ref["cost"][:first], rtol=1e-5)
-        R = cfg.n_rows
-        fl = np.array([ref["lleaf"][k * R:(k + 1) * R] for k in ref["k"]])
-        fr = np.array([ref["rleaf"][k * R:(k + 1) * R] for k in ref["k"]])
+        gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
+        dec.check_unforced(gpu, ref, cfg.n_rows)
         plan.reset()
-        rep = plan.colgen_run(kkt_tol=1e-6, forced=(ref["k"], fl, fr))
-        np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
+        rep = plan.colgen_run(kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, cfg.n_rows))
+    dec.check_replay(rep, ref, cfg.n_rows)
 
 
 # ------------------------------------------------------------------ batched (differentiable) forms
