@@ -99,6 +99,8 @@ typedef struct {
   int64_t master_pg_iters;     /* cumulative projected-gradient iterations */
   int32_t subtile_voxels;      /* voxels per subtile of the aperture-dose columns */
   int32_t n_subtiles;          /* subtiles per column (padded active voxels / subtile_voxels) */
+  int64_t tile_entries[2];     /* union entries of the row tiles of D used by the batched
+                                  products (voxel-major, beamlet-major; 0 until built) */
 } vmat_info;
 
 /* Copy the problem to the device and build every storage form of D:
@@ -293,6 +295,21 @@ typedef enum {
   VMAT_MASTER_PROJECTED_NEWTON = 1
 } vmat_master_method;
 VMAT_API vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method);
+
+/* Arithmetic of the master problem's iterate.  extended = 0 (default): the
+ * dose excess e = z - T of every voxel is an FP32 value carried by the
+ * updates e += t w and recomputed from y every 16th iteration with
+ * compensated sums; gradients are compensated FP32 dot products.  Its
+ * rounding floor lets the relative KKT residual reach about 1e-9.
+ * extended = 1: e, F'(z) and each structure's T, alpha and beta are float
+ * pairs (about 48 bits), the gradient dot products take F' as a pair, and y
+ * moves by exactly the FP32 step and direction that the excess moves by;
+ * the floor drops to about 1e-12 at roughly 1.3x the time per iteration.
+ * For comparisons with an FP64 solver decision by decision.  Available up
+ * to 16 active voxels per master thread (about 1.2M active voxels);
+ * VMAT_EINVAL beyond that or if the variant does not fit an SM.  Read by
+ * every later master launch. */
+VMAT_API vmat_status vmat_set_master_precision(vmat_ctx *ctx, int32_t extended);
 
 /* Price of a beam in the pricing subproblem (Sec. 2.2).  on = 0 (default):
  * the least summed beamlet price of a feasible aperture, as the paper states

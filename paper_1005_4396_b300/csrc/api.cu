@@ -10,9 +10,6 @@
 
 #include "vmat_internal.cuh"
 
-vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
-                              float *g);
-vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act);
 vmat_status vmat_launch_pricing_rec(vmat_ctx *ctx, const float *g, int32_t *rec_k, double *rec_p,
                                     double *rec_p2);
 vmat_status vmat_launch_force(vmat_ctx *ctx, const int32_t *fk, const int16_t *fl,
@@ -219,7 +216,7 @@ extern "C" vmat_status vmat_plan_dose(vmat_ctx *ctx, float *z_dev) {
 vmat_status vmat_enqueue_colgen(vmat_ctx *ctx, int n, int master_max_iters, double kkt_tol,
                                 const Records &rec, bool fresh) {
   for (int t = 0; t < n; ++t) {
-    vmat_status s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g);
+    vmat_status s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g, ctx->master_xp ? ctx->fplo : nullptr);
     if (s != VMAT_OK) return s;
     s = vmat_launch_pricing_rec(ctx, ctx->g, rec.k + t, rec.p + t, rec.p2 + t);
     if (s != VMAT_OK) return s;
@@ -306,7 +303,7 @@ extern "C" vmat_status vmat_colgen_run(vmat_ctx *ctx, const vmat_colgen_opts *o,
   for (int t = 0; t < n && s == VMAT_OK; ++t) {
     mark(t, 0);
     // prices of the free beams from F'(z) of the current plan dose
-    s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g);
+    s = vmat_launch_price(ctx, ctx->fpact, ctx->occ, 2, ctx->g, ctx->master_xp ? ctx->fplo : nullptr);
     if (s != VMAT_OK) break;
     mark(t, 1);
     s = vmat_launch_pricing_rec(ctx, ctx->g, rec.k + t, rec.p + t, rec.p2 + t);

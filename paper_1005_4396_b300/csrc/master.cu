@@ -67,6 +67,7 @@
 
 struct MasterArgs {
   const float *M;
+  const float *Mlo;      // extended precision: [N][Vpad] each column entry minus its FP32 value
   const int32_t *tflag;  // [N][G*VPT/4] nonzero flags of the column subtiles
   int32_t Vpad, nslots, N, cyclic, max_iters, set_rho_plan;
   const int32_t *slot_beam;
@@ -82,6 +83,7 @@ struct MasterArgs {
   unsigned *bar;         // [1] grid barrier word
   int *dstatus;
   float *z_out, *fp_out;  // [Vpad]
+  float *fp_out_lo;       // extended precision: [Vpad] F' minus its FP32 value
   MasterOut *out;
   double *stats;         // [8] cumulative: ns in pass A+reduce, step, pass B, search; syncs; iters
   float *hpart;          // projected Newton: [grid][(N+1)(N+2)/2] per-CTA Gram partials
@@ -155,6 +157,27 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float x) {
 // F'(z) of Eq. 1 from the excess e = z - T of a voxel over its threshold
 __device__ __forceinline__ float dF_e(float e, float al, float be) {
   return e > 0.f ? 2.f * be * e : (e < 0.f ? 2.f * al * e : 0.f);
+}
+
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  const float t = __fadd_rn(a, b);
+  const float bp = __fsub_rn(t, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bp)), __fsub_rn(b, bp));
+  s = t;
+}
+
+// Extended precision: F'(z) = 2 c (eh + el) as a float pair (fh, fl), with
+// the weight c = (ch + cl) of the voxel's side also a pair; the product's
+// rounding error comes from an FMA, the small cross terms go to fl
+__device__ __forceinline__ void dF_pair(float eh, float el, float alh, float all, float beh, float bel,
+                                        float &fh, float &fl) {
+  const bool over = eh > 0.f || (eh == 0.f && el > 0.f);
+  const bool under = eh < 0.f || (eh == 0.f && el < 0.f);
+  const float ch = over ? beh : (under ? alh : 0.f), cl = over ? bel : (under ? all : 0.f);
+  const float c2 = 2.f * ch;  // exact
+  fh = __fmul_rn(c2, eh);
+  fl = __fmaf_rn(c2, eh, -fh) + 2.f * __fmaf_rn(ch, el, cl * eh);
 }
 
 // s + c += a * (bh + bl), compensated: the rounding error of a*bh comes
@@ -402,8 +425,9 @@ __device__ bool chol_packed_aug(float *A, int n, float *cb, float *dg) {
 // this keeps it exact to a few units of its own last place, where plain FP32
 // sums of z would carry errors of the size of T's.
 template <int VPT>
-__device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z,
-                                              const uint32_t (&my_sid)[VPT / 4], const float *s_tab, const int *s_nz, const int *s_mask,
+__device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z, float *zlo,
+                                              const uint32_t (&my_sid)[VPT / 4], const float *s_tab,
+                                              const float *s_tablo, const int *s_nz, const int *s_mask,
                                               const float *s_yf, const float *s_ylo, int nnzs,
                                               size_t off0, size_t mstride) {
   constexpr int NG = VPT / 4;
@@ -411,7 +435,7 @@ __device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z,
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     z[v] = -s_tab[sid_of(my_sid, v)];
-    zc[v] = 0.f;
+    zc[v] = s_tablo ? -s_tablo[sid_of(my_sid, v)] : 0.f;  // extended: T as a float pair
   }
   for (int q = 0; q < nnzs; ++q) {
     const int s = s_nz[q], mk = s_mask[s];
@@ -425,13 +449,26 @@ __device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z,
       dot2_add(z[4 * m + 1], zc[4 * m + 1], c.y, ys, yl);
       dot2_add(z[4 * m + 2], zc[4 * m + 2], c.z, ys, yl);
       dot2_add(z[4 * m + 3], zc[4 * m + 3], c.w, ys, yl);
+      if (zlo) {  // extended precision: the columns' low parts
+        const float4 cl = __ldg((const float4 *)(a.Mlo + (size_t)s * a.Vpad + off0 + m * mstride) +
+                                threadIdx.x);
+        zc[4 * m] = fmaf(cl.x, ys, zc[4 * m]);
+        zc[4 * m + 1] = fmaf(cl.y, ys, zc[4 * m + 1]);
+        zc[4 * m + 2] = fmaf(cl.z, ys, zc[4 * m + 2]);
+        zc[4 * m + 3] = fmaf(cl.w, ys, zc[4 * m + 3]);
+      }
     }
   }
+  if (zlo) {  // extended precision: keep the excess as the pair (z, zlo)
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) z[v] = __fadd_rn(z[v], zc[v]);
+    for (int v = 0; v < VPT; ++v) two_sum(z[v], zc[v], z[v], zlo[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) z[v] = __fadd_rn(z[v], zc[v]);
+  }
 }
 
-template <int VPT, bool NEWTON>
+template <int VPT, bool NEWTON, bool XP>
 __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ns = a.nslots, tid = threadIdx.x, nthr = blockDim.x;
@@ -487,8 +524,17 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   // on the line-search rows (which are zeroed again afterwards)
   float *s_sq = s_fp;                             // [NG][ST]
   float *s_A = s_rows;                            // [max(64 (N+8), (N+1)(N+2)/2)]
+  // extended precision only (the launch sizes it for that variant), after
+  // the last region the variant uses: low parts of F' and of T, alpha, beta
+  float *s_xp = (float *)(((uintptr_t)(NEWTON ? (void *)(s_cb + 2 * (N + 1)) : (void *)(s_mcols + N * NG)) +
+                           15) & ~(uintptr_t)15);
+  float *s_fpl = s_xp;                            // [NG][ST] low part of F' (pass A)
+  float *s_tablo = s_xp + NG * ST;                // [768] T, alpha, beta minus their FP32 values
+  float *s_pplo = s_tablo + 768;                  // [N*NG] low part of each pair's dot product
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
+  if (XP)
+    for (int q = tid; q < 768; q += nthr) s_tablo[q] = (float)(a.tabd[q] - (double)a.tabf[q]);
   for (int q = tid; q < 33 * nthr; q += nthr) s_rows[q] = 0.f;
   for (int k = tid; k < N; k += nthr) {
     s_y[k] = a.y[k];
@@ -545,10 +591,12 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
   for (int m = 0; m < NG; ++m) my_sid[m] = __ldg((const uint32_t *)(a.sid + SUB_OFF(m)) + tid);
   float z[VPT], w[VPT];
+  float zl[XP ? VPT : 1];  // extended precision: low part of the excess
   __syncthreads();
 
   // the dose excess e = M y - T of the thread's voxels
-  excess_from_y<VPT>(a, z, my_sid, s_tab, s_nz, s_mask, s_yf, s_ylo, nnzs, SUB_OFF(0), G * ST);
+  excess_from_y<VPT>(a, z, XP ? zl : nullptr, my_sid, s_tab, XP ? s_tablo : nullptr, s_nz, s_mask,
+                     s_yf, s_ylo, nnzs, SUB_OFF(0), G * ST);
 
   int it = 0, status = VMAT_ENOTCONV, nsync = 0;
   double rho = 0.0, rho0 = 0.0, tol = 0.0;
@@ -569,14 +617,26 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
     for (int m = 0; m < NG; ++m) {
       float4 f;
-      int id = sid_of(my_sid, 4 * m);
-      f.x = dF_e(z[4 * m], s_tab[256 + id], s_tab[512 + id]);
-      id = sid_of(my_sid, 4 * m + 1);
-      f.y = dF_e(z[4 * m + 1], s_tab[256 + id], s_tab[512 + id]);
-      id = sid_of(my_sid, 4 * m + 2);
-      f.z = dF_e(z[4 * m + 2], s_tab[256 + id], s_tab[512 + id]);
-      id = sid_of(my_sid, 4 * m + 3);
-      f.w = dF_e(z[4 * m + 3], s_tab[256 + id], s_tab[512 + id]);
+      if (XP) {
+        float fh[4], fl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int v = 4 * m + q, id = sid_of(my_sid, v);
+          dF_pair(z[v], zl[XP ? v : 0], s_tab[256 + id], s_tablo[256 + id], s_tab[512 + id],
+                  s_tablo[512 + id], fh[q], fl[q]);
+        }
+        f = make_float4(fh[0], fh[1], fh[2], fh[3]);
+        *(float4 *)(s_fpl + m * ST + 4 * tid) = make_float4(fl[0], fl[1], fl[2], fl[3]);
+      } else {
+        int id = sid_of(my_sid, 4 * m);
+        f.x = dF_e(z[4 * m], s_tab[256 + id], s_tab[512 + id]);
+        id = sid_of(my_sid, 4 * m + 1);
+        f.y = dF_e(z[4 * m + 1], s_tab[256 + id], s_tab[512 + id]);
+        id = sid_of(my_sid, 4 * m + 2);
+        f.z = dF_e(z[4 * m + 2], s_tab[256 + id], s_tab[512 + id]);
+        id = sid_of(my_sid, 4 * m + 3);
+        f.w = dF_e(z[4 * m + 3], s_tab[256 + id], s_tab[512 + id]);
+      }
       *(float4 *)(s_fp + m * ST + 4 * tid) = f;
     }
     __syncthreads();
@@ -585,14 +645,29 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       const float4 *Ms = (const float4 *)(a.M + (size_t)s * a.Vpad + SUB_OFF(m));
       const float4 *F4 = (const float4 *)(s_fp + m * ST);
       float acc = 0.f, accc = 0.f;
+      if (XP) {  // F' and the column entries as pairs
+        const float4 *L4 = (const float4 *)(s_fpl + m * ST);
+        const float4 *Ml = (const float4 *)(a.Mlo + (size_t)s * a.Vpad + SUB_OFF(m));
+#pragma unroll 4
+        for (int i = 0; i < lane4; ++i) {
+          const float4 q = __ldg(Ms + lane + 32 * i), ql = __ldg(Ml + lane + 32 * i);
+          const float4 f = F4[lane + 32 * i], fl = L4[lane + 32 * i];
+          dot2_add(acc, accc, q.x, f.x, fl.x);
+          dot2_add(acc, accc, q.y, f.y, fl.y);
+          dot2_add(acc, accc, q.z, f.z, fl.z);
+          dot2_add(acc, accc, q.w, f.w, fl.w);
+          accc = fmaf(ql.x, f.x, fmaf(ql.y, f.y, fmaf(ql.z, f.z, fmaf(ql.w, f.w, accc))));
+        }
+      } else {
 #pragma unroll 8
-      for (int i = 0; i < lane4; ++i) {
-        const float4 q = __ldg(Ms + lane + 32 * i);
-        const float4 f = F4[lane + 32 * i];
-        dot2_add1(acc, accc, q.x, f.x);
-        dot2_add1(acc, accc, q.y, f.y);
-        dot2_add1(acc, accc, q.z, f.z);
-        dot2_add1(acc, accc, q.w, f.w);
+        for (int i = 0; i < lane4; ++i) {
+          const float4 q = __ldg(Ms + lane + 32 * i);
+          const float4 f = F4[lane + 32 * i];
+          dot2_add1(acc, accc, q.x, f.x);
+          dot2_add1(acc, accc, q.y, f.y);
+          dot2_add1(acc, accc, q.z, f.z);
+          dot2_add1(acc, accc, q.w, f.w);
+        }
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
@@ -600,16 +675,31 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         comp_add(acc, accc, s2);
         accc = __fadd_rn(accc, c2);
       }
-      if (lane == 0) s_pp[q] = __fadd_rn(acc, accc);
+      if (lane == 0) {
+        if (XP) {  // the pair's dot product stays a (value, correction) pair
+          two_sum(acc, accc, s_pp[q], s_pplo[q]);
+        } else {
+          s_pp[q] = __fadd_rn(acc, accc);
+        }
+      }
     }
     __syncthreads();
     const int fstride = (N + 3) & ~3;
     float *grow = a.gpart + (size_t)blockIdx.x * fstride;
+    // extended precision: the low parts of the CTA rows follow all G rows
+    float *growlo = a.gpart + (size_t)(G + blockIdx.x) * fstride;
     for (int s = tid; s < ((ns + 3) & ~3); s += nthr) {  // all-zero subtiles contribute exact zeros
       float cs = 0.f, cc = 0.f;
       if (s < ns)
-        for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) comp_add(cs, cc, s_pp[q]);
-      grow[s] = __fadd_rn(cs, cc);
+        for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) {
+          comp_add(cs, cc, s_pp[q]);
+          if (XP) cc = __fadd_rn(cc, s_pplo[q]);
+        }
+      if (XP) {
+        two_sum(cs, cc, grow[s], growlo[s]);
+      } else {
+        grow[s] = __fadd_rn(cs, cc);
+      }
     }
     ++nsync;
     if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
@@ -637,6 +727,19 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
             comp_add(S[2], C[2], xv[u].z);
             comp_add(S[3], C[3], xv[u].w);
           }
+          if (XP) {  // the CTA rows' low parts
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+              const int c = c0 + u * nwarp;
+              const float4 lo = (c < G && j < n4)
+                                    ? __ldcg((const float4 *)(a.gpart + (size_t)(G + c) * fstride) + j)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+              C[0] = __fadd_rn(C[0], lo.x);
+              C[1] = __fadd_rn(C[1], lo.y);
+              C[2] = __fadd_rn(C[2], lo.z);
+              C[3] = __fadd_rn(C[3], lo.w);
+            }
+          }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) s_gw[warp * 128 + 4 * lane + e] = make_float2(S[e], C[e]);
@@ -651,6 +754,20 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           s_g[4 * c4 + t] = (double)gs + (double)gc;  // M^T F'(z) of slot 4 c4 + t
         }
         __syncthreads();
+      }
+    }
+    // the direction pass's first copies (columns of the first own subtile)
+    // do not depend on the step: issue them now so they land during it (the
+    // projected-Newton step stages its Gram chunks in the same region)
+    if (!NEWTON) {
+      const int nm0 = s_mcnt[0];
+      const int *cl0 = s_mcols;
+      const float *src0 = a.M + SUB_OFF(0) + 4 * tid;
+      float4 *pipe0 = (float4 *)s_rows;
+#pragma unroll
+      for (int k = 0; k < master_pipe_stages(VPT); ++k) {
+        if (k < nm0) cp_async16(pipe0 + k * nthr + tid, src0 + (size_t)cl0[k] * a.Vpad);
+        cp_async_commit();
       }
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[0] += c1 - s_clk[4]; s_clk[4] = c1; }
@@ -1038,10 +1155,12 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         const int *cl = s_mcols + m * N;
         const float *src = a.M + SUB_OFF(m) + 4 * tid;
         float4 zz = make_float4(0.f, 0.f, 0.f, 0.f), ww = zz;
+        if (NEWTON || m > 0) {  // (the first subtile's copies went out before the step)
 #pragma unroll
-        for (int k = 0; k < STG; ++k) {
-          if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
-          cp_async_commit();
+          for (int k = 0; k < STG; ++k) {
+            if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
+            cp_async_commit();
+          }
         }
         if (refresh) {
           float4 zc4 = zz;
@@ -1049,6 +1168,12 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           zz.y = -s_tab[sid_of(my_sid, 4 * m + 1)];
           zz.z = -s_tab[sid_of(my_sid, 4 * m + 2)];
           zz.w = -s_tab[sid_of(my_sid, 4 * m + 3)];
+          if (XP) {  // T as a float pair
+            zc4.x = -s_tablo[sid_of(my_sid, 4 * m)];
+            zc4.y = -s_tablo[sid_of(my_sid, 4 * m + 1)];
+            zc4.z = -s_tablo[sid_of(my_sid, 4 * m + 2)];
+            zc4.w = -s_tablo[sid_of(my_sid, 4 * m + 3)];
+          }
           for (int q = 0; q < nm; ++q) {
             cp_async_wait<STG - 1>();
             const int slot = q & (STG - 1);
@@ -1059,11 +1184,26 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
             dot2_add(zz.y, zc4.y, v.y, ys, yl); ww.y = fmaf(v.y, ds, ww.y);
             dot2_add(zz.z, zc4.z, v.z, ys, yl); ww.z = fmaf(v.z, ds, ww.z);
             dot2_add(zz.w, zc4.w, v.w, ys, yl); ww.w = fmaf(v.w, ds, ww.w);
+            if (XP) {  // the columns' low parts
+              const float4 vl =
+                  __ldg((const float4 *)(a.Mlo + SUB_OFF(m) + (size_t)sl * a.Vpad) + tid);
+              zc4.x = fmaf(vl.x, ys, zc4.x); ww.x = fmaf(vl.x, ds, ww.x);
+              zc4.y = fmaf(vl.y, ys, zc4.y); ww.y = fmaf(vl.y, ds, ww.y);
+              zc4.z = fmaf(vl.z, ys, zc4.z); ww.z = fmaf(vl.z, ds, ww.z);
+              zc4.w = fmaf(vl.w, ys, zc4.w); ww.w = fmaf(vl.w, ds, ww.w);
+            }
             if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
             cp_async_commit();
           }
-          z[4 * m] = __fadd_rn(zz.x, zc4.x); z[4 * m + 1] = __fadd_rn(zz.y, zc4.y);
-          z[4 * m + 2] = __fadd_rn(zz.z, zc4.z); z[4 * m + 3] = __fadd_rn(zz.w, zc4.w);
+          if (XP) {
+            two_sum(zz.x, zc4.x, z[4 * m], zl[XP ? 4 * m : 0]);
+            two_sum(zz.y, zc4.y, z[4 * m + 1], zl[XP ? 4 * m + 1 : 0]);
+            two_sum(zz.z, zc4.z, z[4 * m + 2], zl[XP ? 4 * m + 2 : 0]);
+            two_sum(zz.w, zc4.w, z[4 * m + 3], zl[XP ? 4 * m + 3 : 0]);
+          } else {
+            z[4 * m] = __fadd_rn(zz.x, zc4.x); z[4 * m + 1] = __fadd_rn(zz.y, zc4.y);
+            z[4 * m + 2] = __fadd_rn(zz.z, zc4.z); z[4 * m + 3] = __fadd_rn(zz.w, zc4.w);
+          }
         } else {
           for (int q = 0; q < nm; ++q) {
             cp_async_wait<STG - 1>();
@@ -1074,6 +1214,14 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
             ww.y = fmaf(v.y, ds, ww.y);
             ww.z = fmaf(v.z, ds, ww.z);
             ww.w = fmaf(v.w, ds, ww.w);
+            if (XP) {  // the columns' low parts
+              const float4 vl =
+                  __ldg((const float4 *)(a.Mlo + SUB_OFF(m) + (size_t)cl[q] * a.Vpad) + tid);
+              ww.x = fmaf(vl.x, ds, ww.x);
+              ww.y = fmaf(vl.y, ds, ww.y);
+              ww.z = fmaf(vl.z, ds, ww.z);
+              ww.w = fmaf(vl.w, ds, ww.w);
+            }
             if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
             cp_async_commit();
           }
@@ -1203,23 +1351,42 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     // (y as a float pair is read only by the refresh of e in the next
     // direction pass, so it is formed only before such an iteration)
     const bool pair_next = ((it + 1) & 15) == 15;
+    const float tf = (float)t;
     for (int s = tid; s < ns; s += nthr) {
       const int k = s_beam[s];
-      const double dy = t * s_d[k];
+      // extended precision: y moves by exactly the FP32 step and direction
+      // that the excess update below applies (both factors are floats, so
+      // their product is exact in FP64)
+      const double dy = XP ? (double)tf * (double)s_df[s] : t * s_d[k];
       s_dy[s] = dy;
-      s_y[k] = NEWTON ? fmax(s_y[k] + dy, 0.0) : s_y[k] + dy;  // ratio test in FP64: clamp -0
+      if (XP) {  // a full step onto the bound lands on 0 exactly; never below it
+        const double yn = s_y[k] + dy;
+        s_y[k] = (yn <= 0.0 || (t == 1.0 && s_d[k] == -s_y[k])) ? 0.0 : yn;
+      } else {
+        s_y[k] = NEWTON ? fmax(s_y[k] + dy, 0.0) : s_y[k] + dy;  // ratio test in FP64: clamp -0
+      }
       if (pair_next) {
         s_yf[s] = (float)s_y[k];
         s_ylo[s] = (float)(s_y[k] - (double)s_yf[s]);
       }
     }
-    const float tf = (float)t;
+    if (XP) {  // (z, zl) += tf w, the product's rounding error from an FMA
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) z[v] = fmaf(tf, w[v], z[v]);
+      for (int v = 0; v < VPT; ++v) {
+        const float p = __fmul_rn(tf, w[v]), pe = __fmaf_rn(tf, w[v], -p);
+        float sh, se;
+        two_sum(z[v], p, sh, se);
+        two_sum(sh, __fadd_rn(zl[XP ? v : 0], __fadd_rn(se, pe)), z[v], zl[XP ? v : 0]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) z[v] = fmaf(tf, w[v], z[v]);
+    }
     ++it;
     __syncthreads();
   }
 
+  cp_async_wait<0>();  // a solve that stops in the step phase has direction-pass copies in flight
   if (!alive) {
     if (blockIdx.x == 0 && tid == 0) {
       a.out->status = VMAT_ETIMEOUT;
@@ -1235,18 +1402,27 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   double cst = 0.0;
 #pragma unroll
   for (int m = 0; m < NG; ++m) {
-    float zo[4], fo[4];
+    float zo[4], fo[4], flo[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int v = 4 * m + q, id = sid_of(my_sid, v);
       fo[q] = dF_e(z[v], s_tab[256 + id], s_tab[512 + id]);
-      zo[q] = __fadd_rn(z[v], s_tab[id]);
-      // cost against the FP64 threshold: z = e + T in the FP32 threshold, exactly
-      cst += vmat_F((double)z[v] + (double)s_tab[id], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
+      if (XP) {  // z = (eh + el) + T with T = T_hi + T_lo, in FP64; F' as a pair
+        dF_pair(z[v], zl[XP ? v : 0], s_tab[256 + id], s_tablo[256 + id], s_tab[512 + id],
+                s_tablo[512 + id], fo[q], flo[q]);
+        const double zd = ((double)z[v] + (double)zl[XP ? v : 0]) + ((double)s_tab[id] + (double)s_tablo[id]);
+        zo[q] = (float)zd;
+        cst += vmat_F(zd, a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
+      } else {
+        zo[q] = __fadd_rn(z[v], s_tab[id]);
+        // cost against the FP64 threshold: z = e + T in the FP32 threshold, exactly
+        cst += vmat_F((double)z[v] + (double)s_tab[id], a.tabd[id], a.tabd[256 + id], a.tabd[512 + id]);
+      }
     }
     const size_t off = SUB_OFF(m) + 4 * tid;
     *(float4 *)(a.z_out + off) = make_float4(zo[0], zo[1], zo[2], zo[3]);
     *(float4 *)(a.fp_out + off) = make_float4(fo[0], fo[1], fo[2], fo[3]);
+    if (XP) *(float4 *)(a.fp_out_lo + off) = make_float4(flo[0], flo[1], flo[2], flo[3]);
   }
   cst = warp_sum(cst);
   if (lane == 0) s_res[32 + warp] = cst;
@@ -1295,7 +1471,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 }
 
 // ---------------------------------------------------------------- launch
-static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
+static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton, bool xp) {
   const size_t ng = vpt / 4;
   size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
              (size_t)(2 * ((N + 1) & ~1) + ((((N + 1) & ~1) + 3) & ~3) + 768 + LS_POINTS + 16 * 32) * 4 +
@@ -1305,27 +1481,35 @@ static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton) {
              (size_t)(8 + 4 * N + 1 + N * ng) * 4 +            // i beam nz mask pst pair
              (size_t)(8 + N * ng) * 4;                          // per-subtile column lists
   if (newton) b += (size_t)(2 * N + 8 + ng * N) * 4 + (size_t)(2 * N + 2 * (N + 1)) * 4;
+  if (xp) b += 16 + (size_t)nthr * vpt * 4 + 768 * 4 + (size_t)N * ng * 4;  // alignment, low parts:
+                                                                            // F', T/alpha/beta, pairs
   return b + 16;
 }
 
-template <int VPT, bool NEWTON>
-static cudaError_t master_occupancy(int nthr, size_t smem, int *nb) {
-  cudaError_t e = cudaFuncSetAttribute(k_master<VPT, NEWTON>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_master<VPT, NEWTON>, nthr, smem);
+// The master kernel for a launch shape and variant; nullptr where the
+// variant is not built (extended precision stops at 16 voxels per thread).
+static const void *master_fn(int vpt, bool newton, bool xp) {
+#define VMAT_MFN(V)                                                                        \
+  if (vpt == V)                                                                           \
+    return newton ? (xp ? (const void *)k_master<V, true, true> : (const void *)k_master<V, true, false>) \
+                  : (xp ? (const void *)k_master<V, false, true> : (const void *)k_master<V, false, false>);
+  VMAT_MFN(4)
+  VMAT_MFN(8)
+  VMAT_MFN(16)
+#undef VMAT_MFN
+  if (vpt == 32 && !xp) return newton ? (const void *)k_master<32, true, false> : (const void *)k_master<32, false, false>;
+  return nullptr;
 }
 
-static cudaError_t master_occupancy_any(int vpt, bool newton, int nthr, size_t smem, int *nb) {
-  if (newton)
-    return vpt == 4    ? master_occupancy<4, true>(nthr, smem, nb)
-           : vpt == 8  ? master_occupancy<8, true>(nthr, smem, nb)
-           : vpt == 16 ? master_occupancy<16, true>(nthr, smem, nb)
-                       : master_occupancy<32, true>(nthr, smem, nb);
-  return vpt == 4    ? master_occupancy<4, false>(nthr, smem, nb)
-         : vpt == 8  ? master_occupancy<8, false>(nthr, smem, nb)
-         : vpt == 16 ? master_occupancy<16, false>(nthr, smem, nb)
-                     : master_occupancy<32, false>(nthr, smem, nb);
+static cudaError_t master_occupancy_any(int vpt, bool newton, bool xp, int nthr, size_t smem, int *nb) {
+  const void *fn = master_fn(vpt, newton, xp);
+  if (!fn) {
+    *nb = 0;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fn, nthr, smem);
 }
 
 // Launch shape: the fewest voxels per thread (4, 8, 16, 32) that fit the
@@ -1336,7 +1520,9 @@ static cudaError_t master_occupancy_any(int vpt, bool newton, int nthr, size_t s
 // barriers and cross-CTA sums of every iteration cheaper; on B300 ~110 CTAs
 // still stream the columns at full bandwidth, while more voxels per thread
 // (16, 32) lengthen every per-voxel pass.
+#ifndef MASTER_CTA_TARGET
 #define MASTER_CTA_TARGET 112
+#endif
 vmat_status vmat_configure_master(vmat_ctx *ctx) {
   const int64_t Va = ctx->Va > 0 ? ctx->Va : 1;
   const int sms = ctx->sm_budget > 0 && ctx->sm_budget < ctx->num_sms ? ctx->sm_budget : ctx->num_sms;
@@ -1351,10 +1537,15 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   if (nthr > 512 || vpt >= 16) nthr = 512;  // at 16+ voxels per thread every warp counts
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
-  size_t smem = master_smem_bytes(ctx->N, nthr, vpt, false);
-  size_t smem_pn = master_smem_bytes(ctx->N, nthr, vpt, true);
+  const bool xp = ctx->master_xp != 0;
+  if (xp && !master_fn(vpt, false, true))
+    return vmat_fail(ctx, VMAT_EINVAL,
+                     "extended-precision master: at most 16 active voxels per thread (%lld active "
+                     "voxels need %d)", (long long)Va, vpt);
+  size_t smem = master_smem_bytes(ctx->N, nthr, vpt, false, xp);
+  size_t smem_pn = master_smem_bytes(ctx->N, nthr, vpt, true, xp);
   int nb = 0;
-  cudaError_t e = master_occupancy_any(vpt, false, nthr, smem, &nb);
+  cudaError_t e = master_occupancy_any(vpt, false, xp, nthr, smem, &nb);
   if (e != cudaSuccess) return vmat_cuda_fail(ctx, e, "master occupancy");
   if (nb < 1 || grid > nb * ctx->num_sms)
     return vmat_fail(ctx, VMAT_EINVAL, "master kernel cannot be co-resident (%d blocks/SM)", nb);
@@ -1365,7 +1556,7 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
       return vmat_fail(ctx, VMAT_EINVAL,
                        "projected-Newton master needs %zu B of shared memory per CTA (%d beams); "
                        "the device allows %d", smem_pn, ctx->N, optin);
-    e = master_occupancy_any(vpt, true, nthr, smem_pn, &nb);
+    e = master_occupancy_any(vpt, true, xp, nthr, smem_pn, &nb);
     if (e != cudaSuccess) return vmat_cuda_fail(ctx, e, "projected-Newton master occupancy");
     if (nb < 1 || grid > nb * ctx->num_sms)
       return vmat_fail(ctx, VMAT_EINVAL, "projected-Newton master cannot be co-resident");
@@ -1380,9 +1571,10 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
 }
 
 // doubles: per-CTA partial rows [grid][N + PART_EXTRA], then (16-byte
-// aligned) the per-CTA gradient partial rows [grid][(N+3)&~3] floats
+// aligned) the per-CTA gradient partial rows [2 * grid][(N+3)&~3] floats
 int64_t vmat_master_scratch(int grid, int N) {
-  return (int64_t)grid * (N + PART_EXTRA) + 2 + ((int64_t)grid * ((N + 3) & ~3) + 1) / 2;
+  // the gradient rows twice: value rows, then (extended precision) their low parts
+  return (int64_t)grid * (N + PART_EXTRA) + 2 + ((int64_t)2 * grid * ((N + 3) & ~3) + 1) / 2;
 }
 
 int64_t vmat_hessian_len(int N) { return (int64_t)(N + 1) * (N + 2) / 2; }
@@ -1418,6 +1610,10 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   a.dstatus = ctx->dstatus;
   a.z_out = ctx->zact;
   a.fp_out = ctx->fpact;
+  a.Mlo = ctx->master_xp ? ctx->Mlo : nullptr;
+  a.fp_out_lo = ctx->master_xp ? ctx->fplo : nullptr;
+  if (ctx->master_xp && (!ctx->Mlo || !ctx->fplo))
+    return vmat_fail(ctx, VMAT_ESTATE, "extended-precision buffers missing");
   a.out = ctx->mout;
   a.stats = ctx->mstats;
   const bool pn = ctx->master_method == VMAT_MASTER_PROJECTED_NEWTON;
@@ -1435,15 +1631,8 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, ctx->stream));
   void *args[] = {&a};
   dim3 grid(ctx->master_grid), block(ctx->master_block);
-  const int v = ctx->master_vpt;
-  const void *fn = pn ? (v == 4    ? (const void *)k_master<4, true>
-                         : v == 8  ? (const void *)k_master<8, true>
-                         : v == 16 ? (const void *)k_master<16, true>
-                                   : (const void *)k_master<32, true>)
-                      : (v == 4    ? (const void *)k_master<4, false>
-                         : v == 8  ? (const void *)k_master<8, false>
-                         : v == 16 ? (const void *)k_master<16, false>
-                                   : (const void *)k_master<32, false>);
+  const void *fn = master_fn(ctx->master_vpt, pn, ctx->master_xp != 0);
+  if (!fn) return vmat_fail(ctx, VMAT_EINVAL, "no master kernel for this launch shape and precision");
   const size_t smem = pn ? ctx->master_smem_pn : ctx->master_smem;
   // the dynamic shared-memory limit is a per-kernel, process-wide attribute:
   // set it for this context's launch (another context may have lowered it)

@@ -223,6 +223,7 @@ static std::vector<double> plan_settings(const vmat_batch *b) {
   for (const vmat_ctx *c : b->plans) {
     v.push_back(c->gamma);
     v.push_back(c->master_method);
+    v.push_back(c->master_xp);
     v.push_back(c->price_smoothing);
   }
   return v;

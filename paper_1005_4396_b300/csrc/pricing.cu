@@ -15,7 +15,8 @@
 // k_select: least aperture price over free beams (ties: lowest beam), and
 // the least price of the others.
 // k_aperture: M[:, slot] = sum over open beamlets of the chosen aperture of
-// D_i,: , by one thread per voxel over its voxel-major row (sorted by
+// D_i,: (in FP32; with the extended-precision master in FP64 and kept as a
+// float pair), by one thread per voxel over its voxel-major row (sorted by
 // beamlet, so the beam's entries are one contiguous run found by bisection).
 #include <math.h>
 
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
                                                   const SelRec *__restrict__ sel,
                                                   const int16_t *__restrict__ sl,
                                                   const int16_t *__restrict__ sr,
-                                                  float *__restrict__ Mcol, int tile,
+                                                  float *__restrict__ Mcol,
+                                                  float *__restrict__ Mcol_lo, int tile,
                                                   int32_t *__restrict__ tflag) {
   __shared__ int16_t L[VMAT_MAX_ROWS], Rr[VMAT_MAX_ROWS];
   __shared__ int sk;
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
   const int k = sk;
   if (a >= Va || k < 0) {
     Mcol[a] = 0.f;
+    if (Mcol_lo) Mcol_lo[a] = 0.f;
     return;  // padding and failed selections leave the tile flags alone
   }
   const int32_t RC = R * C, lo = k * RC, hi = lo + RC;
@@ -271,20 +274,26 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
     else e = m;
   }
   const int64_t end = ptr[a + 1];
-  float acc = 0.f;
+  float accf = 0.f;   // FP32 sum in beamlet order
+  double acc = 0.0;   // extended precision: FP64 sum, kept as a float pair
   for (int64_t q = b; q < end; ++q) {
     const int32_t i = col[q];
     if (i >= hi) break;
     const int32_t rc = i - lo, row = rc / C, c = rc - row * C;
     if (c >= L[row] && c < Rr[row]) {
-      float v = vmat_ld(val, q);
-      acc += use_scale ? v * scale[i] : v;
+      const float v = vmat_ld(val, q);
+      if (Mcol_lo) acc += use_scale ? (double)v * (double)scale[i] : (double)v;
+      else accf += use_scale ? v * scale[i] : v;
     }
   }
-  Mcol[a] = acc;
+  if (Mcol_lo) {
+    accf = (float)acc;
+    Mcol_lo[a] = (float)(acc - (double)accf);
+  }
+  Mcol[a] = accf;
   // mark the master subtile holding voxel a as nonzero for this column
   // (subtiles are whole multiples of 128 voxels: a warp never straddles two)
-  if (__any_sync(__activemask(), acc != 0.f) && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
+  if (__any_sync(__activemask(), accf != 0.f) && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
     atomicOr(tflag + a / tile, 1);
 }
 
@@ -322,6 +331,7 @@ __global__ void k_commit(const SelRec *sel, const int16_t *sl, const int16_t *sr
 vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot, int32_t *rec_subtiles) {
   cudaStream_t st = ctx->stream;
   float *Mcol = ctx->M + (size_t)slot * ctx->Vpad;
+  float *Mcol_lo = ctx->Mlo ? ctx->Mlo + (size_t)slot * ctx->Vpad : nullptr;
   const int nsub = ctx->master_grid * (ctx->master_vpt / 4);
   int32_t *tf = ctx->tflag + (size_t)slot * nsub;
   const int tile = ctx->master_block * 4;  // master subtile
@@ -330,7 +340,7 @@ vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot, int32_t *rec_subtile
   int us = ctx->dt != VMAT_F32;
 #define VMAT_AP_ARGS                                                                              \
   ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, ctx->Va, ctx->Vpad, ctx->R, \
-      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol, tile, tf
+      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol, Mcol_lo, tile, tf
   if (ctx->dt == VMAT_F32) {
     typedef float TV;
     k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);

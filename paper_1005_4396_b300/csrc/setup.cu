@@ -267,6 +267,8 @@ static vmat_status build_storage(vmat_ctx *ctx, Tmp &tmp, const int32_t *colv, c
 // Buffers whose size follows the master kernel's tiling (padded voxel count,
 // grid): structure ids of the active voxels, the aperture-dose matrix and its
 // subtile flags, plan dose and derivative, reduction scratch.
+static vmat_status alloc_xp(vmat_ctx *ctx);
+
 static vmat_status alloc_tiled(vmat_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   const int32_t Vpad = ctx->Vpad;
@@ -291,10 +293,38 @@ static vmat_status alloc_tiled(vmat_ctx *ctx) {
     ctx->hbuf_len = (int64_t)(ctx->master_grid + 1) * vmat_hessian_len(N);
     VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->hbuf, ctx->hbuf_len));
   }
+  if (ctx->master_xp) return alloc_xp(ctx);
   return VMAT_OK;
 }
 
+// Extended-precision master: the low parts of the columns and of F'.
+static vmat_status alloc_xp(vmat_ctx *ctx) {
+  if (!ctx->Mlo) {
+    VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->Mlo, (size_t)ctx->N * ctx->Vpad));
+    VMAT_CUDA(ctx, cudaMemsetAsync(ctx->Mlo, 0, (size_t)ctx->N * ctx->Vpad * 4, ctx->stream));
+  }
+  if (!ctx->fplo) {
+    VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->fplo, (size_t)ctx->Vpad));
+    VMAT_CUDA(ctx, cudaMemsetAsync(ctx->fplo, 0, (size_t)ctx->Vpad * 4, ctx->stream));
+  }
+  return VMAT_OK;
+}
+
+static void free_xp(vmat_ctx *ctx) {
+  if (ctx->Mlo) {
+    cudaFree(ctx->Mlo);
+    ctx->Mlo = nullptr;
+    ctx->device_bytes -= (int64_t)ctx->N * ctx->Vpad * 4;
+  }
+  if (ctx->fplo) {
+    cudaFree(ctx->fplo);
+    ctx->fplo = nullptr;
+    ctx->device_bytes -= (int64_t)ctx->Vpad * 4;
+  }
+}
+
 static void free_tiled(vmat_ctx *ctx) {
+  free_xp(ctx);
   void **ptrs[] = {(void **)&ctx->sid, (void **)&ctx->M, (void **)&ctx->tflag, (void **)&ctx->zact,
                    (void **)&ctx->fpact, (void **)&ctx->fgather, (void **)&ctx->red};
   size_t bytes[] = {(size_t)ctx->Vpad, (size_t)ctx->N * ctx->Vpad * 4,
@@ -352,6 +382,27 @@ extern "C" vmat_status vmat_set_master_method(vmat_ctx *ctx, int32_t method) {
     VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->hbuf, ctx->hbuf_len));
   }
   return VMAT_OK;
+}
+
+extern "C" vmat_status vmat_set_master_precision(vmat_ctx *ctx, int32_t extended) {
+  if (!ctx) return VMAT_EINVAL;
+  if (extended != 0 && extended != 1)
+    return vmat_fail(ctx, VMAT_EINVAL, "master precision must be 0 (FP32) or 1 (extended)");
+  if (extended == ctx->master_xp) return VMAT_OK;
+  if (ctx->n_slots != 0)
+    return vmat_fail(ctx, VMAT_EINVAL, "the plan has columns: call vmat_reset first");
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int old = ctx->master_xp;
+  ctx->master_xp = extended;
+  vmat_status s = vmat_configure_master(ctx);  // same tiling; checks the variant fits an SM
+  if (s == VMAT_OK && extended) s = alloc_xp(ctx);
+  if (s != VMAT_OK) {
+    ctx->master_xp = old;
+    vmat_configure_master(ctx);
+    return s;
+  }
+  if (!extended) free_xp(ctx);
+  return vmat_reset(ctx);  // F' of the empty plan in the new form
 }
 
 extern "C" vmat_status vmat_set_price_smoothing(vmat_ctx *ctx, int32_t on) {
@@ -521,6 +572,9 @@ extern "C" vmat_status vmat_create(const vmat_problem *P, vmat_dtype dt, void *s
 extern "C" void vmat_destroy(vmat_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  vmat_free_row_tiles(ctx, ctx->vtiles);
+  vmat_free_row_tiles(ctx, ctx->btiles);
+  free_xp(ctx);
   void *ptrs[] = {ctx->fa32, ctx->act_vox, ctx->vox2act, ctx->sid_full, ctx->sid, ctx->tabf, ctx->tabd,
                   ctx->theta, ctx->scale, ctx->bm_ptr, ctx->bm_col, ctx->bm_val, ctx->vm_ptr,
                   ctx->vm_col, ctx->vm_val, ctx->M, ctx->tflag, ctx->occ, ctx->lleaf, ctx->rleaf,
@@ -556,18 +610,26 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
   for (int q = 0; q < 4; ++q) out->master_ms[q] = ms[q] * 1e-6;
   out->master_syncs = (int64_t)ms[4];
   out->master_pg_iters = (int64_t)ms[5];
+  out->tile_entries[0] = ctx->vtiles.n_union;
+  out->tile_entries[1] = ctx->btiles.n_union;
   out->subtile_voxels = ctx->master_block * 4;
   out->n_subtiles = ctx->master_grid * (ctx->master_vpt / 4);
   return VMAT_OK;
 }
 
-__global__ void k_init_fprime(const uint8_t *sid, const float *tab, int32_t Vpad, float *z,
-                              float *fp) {
+__global__ void k_init_fprime(const uint8_t *sid, const float *tab, const double *tabd, int32_t Vpad,
+                              float *z, float *fp, float *fplo) {
   int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= Vpad) return;
   int q = sid[a];
   z[a] = 0.f;
-  fp[a] = vmat_dF(0.f, tab[q], tab[256 + q], tab[512 + q]);
+  if (fplo) {  // extended precision: F'(0) = -2 alpha T in FP64, as a float pair
+    const double f = -2.0 * tabd[256 + q] * tabd[q];
+    fp[a] = (float)f;
+    fplo[a] = (float)(f - (double)(float)f);
+  } else {
+    fp[a] = vmat_dF(0.f, tab[q], tab[256 + q], tab[512 + q]);
+  }
 }
 
 // Clear the plan state on the context's stream without waiting (usable while
@@ -583,8 +645,9 @@ vmat_status vmat_enqueue_reset(vmat_ctx *ctx) {
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->y, 0, (size_t)N * 8, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->rho_plan, 0, 8, st));
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->dstatus, 0, 4, st));
-  k_init_fprime<<<(ctx->Vpad + 255) / 256, 256, 0, st>>>(ctx->sid, ctx->tabf, ctx->Vpad, ctx->zact,
-                                                          ctx->fpact);
+  k_init_fprime<<<(ctx->Vpad + 255) / 256, 256, 0, st>>>(ctx->sid, ctx->tabf, ctx->tabd, ctx->Vpad,
+                                                          ctx->zact, ctx->fpact,
+                                                          ctx->master_xp ? ctx->fplo : nullptr);
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 1;
   ctx->n_slots = 0;

@@ -4,7 +4,7 @@
 //   dose   z_j = sum_i Dhat_ij (s_i x_i)     voxel-major CSR, warp per row,
 //          fused epilogue: F'(z_j) and the FP64 cost sum_j F(z_j) (Eq. 1)
 //   batched forms over 32 fluence vectors (lane = vector) for the
-//   differentiable forward and its adjoint.
+//   differentiable forward and its adjoint, on row tiles of D (tiles.cu).
 // D is streamed once per call (16-byte loads, evict-first); the dense vector
 // that is gathered (f or x, at most a few MB) stays resident in L2.
 // Dhat = D for FP32 storage; F16/BF16 store D_ij / s_i.
@@ -88,6 +88,34 @@ __global__ void __launch_bounds__(256) k_price(const int64_t *__restrict__ ptr,
   if (lane == 0) g[i] = use_scale ? acc * scale[i] : acc;
 }
 
+// Extended precision (the master's F' as the pair f + flo): g_i = s_i *
+// sum_j Dhat_ij (f_j + flo_j) accumulated in FP64, one warp per row, lanes
+// combined in a fixed order; g is rounded to FP32 once.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price_xp(const int64_t *__restrict__ ptr,
+                                                  const int32_t *__restrict__ col,
+                                                  const TV *__restrict__ val,
+                                                  const float *__restrict__ scale, int use_scale,
+                                                  const float *__restrict__ f,
+                                                  const float *__restrict__ flo,
+                                                  const uint8_t *__restrict__ mask, int mode, int RC,
+                                                  int64_t B, float *__restrict__ g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (i >= B) return;
+  if (mode) {
+    bool m = mask[i / RC] != 0;
+    if (m != (mode == 1)) return;
+  }
+  double acc = 0.0;
+  for (int64_t e = __ldg(ptr + i) + lane; e < __ldg(ptr + i + 1); e += 32) {
+    const int32_t c = __ldcs(col + e);
+    acc = fma((double)ld_stream(val, e), (double)__ldg(f + c) + (double)__ldg(flo + c), acc);
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) g[i] = (float)(use_scale ? acc * (double)scale[i] : acc);
+}
+
 __global__ void k_gather_active(const float *__restrict__ full, const int32_t *__restrict__ act,
                                 int32_t Va, int32_t Vpad, float *__restrict__ out) {
   int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,12 +123,24 @@ __global__ void k_gather_active(const float *__restrict__ full, const int32_t *_
 }
 
 vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
-                              float *g) {
+                              float *g, const float *f_lo) {
   const int64_t B = ctx->B;
   unsigned nb = (unsigned)((B + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
   const int RC = ctx->R * ctx->C;
   int us = ctx->dt != VMAT_F32;
-  if (ctx->dt == VMAT_F32)
+  if (f_lo) {
+    if (ctx->dt == VMAT_F32)
+      k_price_xp<float><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
+                                                     ctx->scale, us, f_act, f_lo, mask, mode, RC, B, g);
+    else if (ctx->dt == VMAT_F16)
+      k_price_xp<__half><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col, (const __half *)ctx->bm_val,
+                                                      ctx->scale, us, f_act, f_lo, mask, mode, RC, B, g);
+    else
+      k_price_xp<__nv_bfloat16><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col,
+                                                             (const __nv_bfloat16 *)ctx->bm_val,
+                                                             ctx->scale, us, f_act, f_lo, mask, mode,
+                                                             RC, B, g);
+  } else if (ctx->dt == VMAT_F32)
     k_price<float><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
                                                 ctx->scale, us, f_act, mask, mode, RC, B, g);
   else if (ctx->dt == VMAT_F16)
@@ -227,63 +267,140 @@ vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float
 }
 
 // ---------------------------------------------------------------- batched (32 vectors)
-// Z[a][b] = sum_e Dhat[e] * X[col[e]][b]: the warp loads 32 entries of the
-// row at once and broadcasts each; lane b owns vector b.
-template <typename TV>
-__device__ __forceinline__ float warp_row_dot32(const int32_t *__restrict__ col,
-                                                const TV *__restrict__ val,
-                                                const float *__restrict__ X,
-                                                const float *__restrict__ colscale, int64_t e0,
-                                                int64_t e1, int lane) {
-  float acc = 0.f;
-  for (int64_t e = e0; e < e1; e += 32) {
-    int n = (int)min((int64_t)32, e1 - e);
-    int32_t c = 0;
-    float v = 0.f;
-    if (lane < n) {
-      c = __ldcs(col + e + lane);
-      v = ld_stream(val, e + lane);
-      if (colscale) v *= __ldg(colscale + c);
-    }
-    for (int q = 0; q < n; ++q) {
-      int32_t cq = __shfl_sync(0xffffffffu, c, q);
-      float vq = __shfl_sync(0xffffffffu, v, q);
-      acc = fmaf(vq, __ldg(X + (size_t)cq * 32 + lane), acc);
-    }
+// 8 consecutive values (one union entry of a row tile, 16- or 32-byte aligned)
+__device__ __forceinline__ void load8(const float *p, float (&v)[8]) {
+  const float4 a = __ldcs((const float4 *)p), b = __ldcs((const float4 *)p + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __half *p, float (&v)[8]) {
+  const uint4 u = __ldcs((const uint4 *)p);
+  const __half2 *h = (const __half2 *)&u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = __half22float2(h[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
   }
-  return acc;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16 *p, float (&v)[8]) {
+  const uint4 u = __ldcs((const uint4 *)p);
+  const __nv_bfloat162 *h = (const __nv_bfloat162 *)&u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
+// Row-tiled batched product (tiles.cu): one warp per tile of 8 rows, lane =
+// vector.  The warp stages 32 union entries at a time (column, 8 values as
+// floats, times the column's scale for reduced-precision dose) in shared
+// memory, then for each entry gathers the dense operand's 128-byte row once
+// and updates all 8 rows; each row sums its own entries in the CSR's
+// column order.
+template <typename TV>
+__device__ __forceinline__ void tile_rows32(const RowTiles &t, const TV *__restrict__ uval,
+                                            const float *__restrict__ colscale,
+                                            const float *__restrict__ X, int64_t tile, int lane,
+                                            int32_t *s_c, float4 *s_v, float (&acc)[8]) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+  const int64_t e0 = t.uptr[tile], e1 = t.uptr[tile + 1];
+  for (int64_t base = e0; base < e1; base += 32) {
+    const int n = (int)min((int64_t)32, e1 - base);
+    if (lane < n) {
+      const int32_t c = __ldcs(t.ucol + base + lane);
+      float v[8];
+      load8(uval + (base + lane) * 8, v);
+      if (colscale) {
+        const float sc = __ldg(colscale + c);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] *= sc;
+      }
+      s_c[lane] = c;
+      s_v[2 * lane] = make_float4(v[0], v[1], v[2], v[3]);
+      s_v[2 * lane + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      const float x = __ldg(X + (size_t)s_c[q] * 32 + lane);
+      const float4 a = s_v[2 * q], b = s_v[2 * q + 1];
+      acc[0] = fmaf(a.x, x, acc[0]);
+      acc[1] = fmaf(a.y, x, acc[1]);
+      acc[2] = fmaf(a.z, x, acc[2]);
+      acc[3] = fmaf(a.w, x, acc[3]);
+      acc[4] = fmaf(b.x, x, acc[4]);
+      acc[5] = fmaf(b.y, x, acc[5]);
+      acc[6] = fmaf(b.z, x, acc[6]);
+      acc[7] = fmaf(b.w, x, acc[7]);
+    }
+    __syncwarp();
+  }
 }
 
 template <typename TV>
-__global__ void __launch_bounds__(256) k_dose32(const int64_t *__restrict__ ptr,
-                                                const int32_t *__restrict__ col,
-                                                const TV *__restrict__ val,
-                                                const float *__restrict__ scale, int use_scale,
-                                                const float *__restrict__ X, int32_t Va,
-                                                const int32_t *__restrict__ act,
-                                                const uint8_t *__restrict__ sid,
-                                                const float *__restrict__ tabf,
-                                                const double *__restrict__ tabd, float *Z,
-                                                float *Fp, double *part) {
+__global__ void __launch_bounds__(256) k_dose32t(RowTiles t, const float *__restrict__ scale,
+                                                 int use_scale, const float *__restrict__ X,
+                                                 int32_t Va, const int32_t *__restrict__ act,
+                                                 const uint8_t *__restrict__ sid,
+                                                 const float *__restrict__ tabf,
+                                                 const double *__restrict__ tabd, float *Z,
+                                                 float *Fp, double *part) {
+  __shared__ int32_t s_c[WARPS_PER_BLOCK][32];
+  __shared__ float4 s_v[WARPS_PER_BLOCK][64];
   __shared__ double s_cost[WARPS_PER_BLOCK][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int32_t a = blockIdx.x * WARPS_PER_BLOCK + warp;
+  const int64_t tile = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
   double c = 0.0;
-  if (a < Va) {
-    float z = warp_row_dot32<TV>(col, val, X, use_scale ? scale : nullptr, __ldg(ptr + a),
-                                 __ldg(ptr + a + 1), lane);
-    int q = sid[a];
-    size_t j = (size_t)act[a];
-    Z[j * 32 + lane] = z;
-    if (Fp) Fp[j * 32 + lane] = vmat_dF(z, tabf[q], tabf[256 + q], tabf[512 + q]);
-    c = vmat_F((double)z, tabd[q], tabd[256 + q], tabd[512 + q]);
+  if (tile < t.n_tiles) {
+    float acc[8];
+    tile_rows32<TV>(t, (const TV *)t.uval, use_scale ? scale : nullptr, X, tile, lane, s_c[warp],
+                    s_v[warp], acc);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t a = tile * 8 + r;
+      if (a < Va) {
+        const int q = sid[a];
+        const size_t j = (size_t)act[a];
+        Z[j * 32 + lane] = acc[r];
+        if (Fp) Fp[j * 32 + lane] = vmat_dF(acc[r], tabf[q], tabf[256 + q], tabf[512 + q]);
+        c += vmat_F((double)acc[r], tabd[q], tabd[256 + q], tabd[512 + q]);
+      }
+    }
   }
   s_cost[warp][lane] = c;
   __syncthreads();
   if (part && threadIdx.x < 32) {
-    double s = 0.0;
-    for (int w = 0; w < WARPS_PER_BLOCK; ++w) s += s_cost[w][threadIdx.x];
-    part[(size_t)blockIdx.x * 32 + threadIdx.x] = s;
+    double sum = 0.0;
+    for (int w = 0; w < WARPS_PER_BLOCK; ++w) sum += s_cost[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 32 + threadIdx.x] = sum;
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price32t(RowTiles t, const float *__restrict__ scale,
+                                                  int use_scale, const float *__restrict__ Fa,
+                                                  int64_t B, const float *__restrict__ colw,
+                                                  float *__restrict__ G) {
+  __shared__ int32_t s_c[WARPS_PER_BLOCK][32];
+  __shared__ float4 s_v[WARPS_PER_BLOCK][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
+  if (tile >= t.n_tiles) return;
+  float acc[8];
+  tile_rows32<TV>(t, (const TV *)t.uval, nullptr, Fa, tile, lane, s_c[warp], s_v[warp], acc);
+  const float cw = colw ? colw[lane] : 1.f;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = tile * 8 + r;
+    if (i < B) {
+      float g = acc[r];
+      if (use_scale) g *= scale[i];
+      if (colw) g *= cw;
+      G[(size_t)i * 32 + lane] = g;
+    }
   }
 }
 
@@ -314,23 +431,6 @@ __global__ void k_sum_partials32(const double *__restrict__ part, int64_t nb, do
   }
 }
 
-template <typename TV>
-__global__ void __launch_bounds__(256) k_price32(const int64_t *__restrict__ ptr,
-                                                 const int32_t *__restrict__ col,
-                                                 const TV *__restrict__ val,
-                                                 const float *__restrict__ scale, int use_scale,
-                                                 const float *__restrict__ Fa, int64_t B,
-                                                 const float *__restrict__ colw,
-                                                 float *__restrict__ G) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-  if (i >= B) return;
-  float acc = warp_row_dot32<TV>(col, val, Fa, nullptr, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
-  if (use_scale) acc *= scale[i];
-  if (colw) acc *= colw[lane];
-  G[(size_t)i * 32 + lane] = acc;
-}
-
 __global__ void k_gather_active32(const float *__restrict__ full, const int32_t *__restrict__ act,
                                   int32_t Va, float *__restrict__ out) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,18 +446,24 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
   if ((int64_t)nb * 32 + 64 > ctx->red_len) return vmat_fail(ctx, VMAT_EINVAL, "scratch too small");
   double *part = cost_dev ? ctx->red : nullptr;
   int us = ctx->dt != VMAT_F32;
-#define VMAT_D32_ARGS                                                                        \
-  ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, X, ctx->Va, ctx->act_vox, \
-      ctx->sid, ctx->tabf, ctx->tabd, Z, Fp, part
+  vmat_status ts = vmat_ensure_row_tiles(ctx, true);
+  if (ts != VMAT_OK) return ts;
+  // one block per 8 tiles of 8 active voxels: fewer partial rows than the
+  // warp-per-voxel form, so the scratch check above covers them
+  nb = (unsigned)((ctx->vtiles.n_tiles + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  if (nb == 0) nb = 1;
+#define VMAT_D32_ARGS                                                                    \
+  ctx->vtiles, ctx->scale, us, X, ctx->Va, ctx->act_vox, ctx->sid, ctx->tabf, ctx->tabd, Z, \
+      Fp, part
   if (ctx->dt == VMAT_F32) {
     typedef float TV;
-    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+    k_dose32t<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
   } else if (ctx->dt == VMAT_F16) {
     typedef __half TV;
-    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+    k_dose32t<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
   } else {
     typedef __nv_bfloat16 TV;
-    k_dose32<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
+    k_dose32t<TV><<<nb, 256, 0, st>>>(VMAT_D32_ARGS);
   }
 #undef VMAT_D32_ARGS
   k_fill_inactive32<<<(unsigned)(((int64_t)ctx->V * 32 + 255) / 256), 256, 0, st>>>(
@@ -374,18 +480,17 @@ vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const floa
   float *Fa = ctx->fa32;
   k_gather_active32<<<(unsigned)(((int64_t)ctx->Va * 32 + 255) / 256 + 1), 256, 0, st>>>(
       Fp, ctx->act_vox, ctx->Va, Fa);
-  unsigned nb = (unsigned)((ctx->B + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  vmat_status ts = vmat_ensure_row_tiles(ctx, false);
+  if (ts != VMAT_OK) return ts;
+  unsigned nb = (unsigned)((ctx->btiles.n_tiles + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  if (nb == 0) nb = 1;
   int us = ctx->dt != VMAT_F32;
   if (ctx->dt == VMAT_F32)
-    k_price32<float><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
-                                         ctx->scale, us, Fa, ctx->B, colw, G);
+    k_price32t<float><<<nb, 256, 0, st>>>(ctx->btiles, ctx->scale, us, Fa, ctx->B, colw, G);
   else if (ctx->dt == VMAT_F16)
-    k_price32<__half><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const __half *)ctx->bm_val,
-                                          ctx->scale, us, Fa, ctx->B, colw, G);
+    k_price32t<__half><<<nb, 256, 0, st>>>(ctx->btiles, ctx->scale, us, Fa, ctx->B, colw, G);
   else
-    k_price32<__nv_bfloat16><<<nb, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col,
-                                                 (const __nv_bfloat16 *)ctx->bm_val, ctx->scale,
-                                                 us, Fa, ctx->B, colw, G);
+    k_price32t<__nv_bfloat16><<<nb, 256, 0, st>>>(ctx->btiles, ctx->scale, us, Fa, ctx->B, colw, G);
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 2;
   return VMAT_OK;

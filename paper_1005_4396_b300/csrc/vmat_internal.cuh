@@ -32,6 +32,16 @@ struct MasterOut {
   int32_t iters, status;
 };
 
+// Rows [8 t, 8 t + 8) of a CSR as the sorted union of their column indices
+// and a dense [|U|][8] value block (0 where a row has no entry); built on
+// the first batched product that needs it (tiles.cu).
+struct RowTiles {
+  int64_t n_tiles = 0, n_union = 0;
+  int64_t *uptr = nullptr;  // [n_tiles + 1] first union entry of each tile
+  int32_t *ucol = nullptr;  // [n_union] column index
+  void *uval = nullptr;     // [n_union][8] values in the storage type of D
+};
+
 struct vmat_ctx {
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
@@ -65,6 +75,7 @@ struct vmat_ctx {
 
   // plan state
   float *M = nullptr;          // [N][Vpad] aperture-dose columns in order of addition
+  float *Mlo = nullptr;        // [N][Vpad] extended precision: each entry minus its FP32 value
   int32_t *tflag = nullptr;    // [N][master_grid*vpt/4] 1 if column s is nonzero in master subtile
   uint8_t *occ = nullptr;      // [N]
   int16_t *lleaf = nullptr, *rleaf = nullptr;  // [N*R]
@@ -73,6 +84,7 @@ struct vmat_ctx {
   double *y = nullptr;         // [N]
   float *zact = nullptr;       // [Vpad] plan dose on active voxels
   float *fpact = nullptr;      // [Vpad] F'(z) of the plan dose
+  float *fplo = nullptr;       // [Vpad] extended precision: F' minus its FP32 value
   double *rho_plan = nullptr;  // [1] residual at the start of the plan's first master solve
 
   // workspaces
@@ -80,6 +92,7 @@ struct vmat_ctx {
   float *fgather = nullptr;    // [Vpad] caller vector gathered onto active voxels
   float *xs = nullptr;         // [B] scaled fluence for reduced-precision dose
   float *fa32 = nullptr;       // [Va*32] batched adjoint input on active voxels (lazy)
+  RowTiles vtiles, btiles;     // row tiles of the voxel-major and beamlet-major CSR (lazy)
   double *ap_price = nullptr;  // [N] best aperture price per beam
   int16_t *ap_l = nullptr, *ap_r = nullptr;  // [N*R] best leaves per beam
   SelRec *sel = nullptr;       // [1]
@@ -99,6 +112,7 @@ struct vmat_ctx {
   int profiling = 0;
   int sm_budget = 0;           // master kernel CTA budget (0: every SM)
   int master_method = 0;       // VMAT_MASTER_PROJECTED_GRADIENT or _NEWTON
+  int master_xp = 0;           // 1: extended-precision master (float-pair dose excess and F')
   size_t master_smem_pn = 0;   // shared memory of the projected-Newton variant
   float *hbuf = nullptr;       // projected Newton: [grid + 1][(N+1)(N+2)/2] Gram partials + sum
   int64_t hbuf_len = 0;
@@ -147,7 +161,7 @@ __device__ __forceinline__ float vmat_ld(const __nv_bfloat16 *p, int64_t e) {
 
 // Launchers implemented in the .cu files.
 vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
-                              float *g);
+                              float *g, const float *f_lo = nullptr);
 vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act);
 vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float *fp_full,
                              double *cost_dev);
@@ -160,6 +174,8 @@ vmat_status vmat_launch_dose_batch32(vmat_ctx *ctx, const float *X, float *Z, fl
                                      double *cost_dev);
 vmat_status vmat_launch_price_batch32(vmat_ctx *ctx, const float *Fp, const float *colw, float *G);
 vmat_status vmat_configure_master(vmat_ctx *ctx);
+vmat_status vmat_ensure_row_tiles(vmat_ctx *ctx, bool voxel_major);
+void vmat_free_row_tiles(vmat_ctx *ctx, RowTiles &t);
 int64_t vmat_master_scratch(int grid, int N);
 int64_t vmat_hessian_len(int N);
 vmat_status vmat_enqueue_reset(vmat_ctx *ctx);

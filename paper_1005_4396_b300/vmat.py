@@ -50,7 +50,7 @@ class vmat_info(ctypes.Structure):
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
                 ("master_block", _i32), ("n_launches", _i64), ("master_ms", _d * 4),
                 ("master_syncs", _i64), ("master_pg_iters", _i64), ("subtile_voxels", _i32),
-                ("n_subtiles", _i32)]
+                ("n_subtiles", _i32), ("tile_entries", _i64 * 2)]
 
 
 class vmat_column(ctypes.Structure):
@@ -101,6 +101,7 @@ EXPORTS = {
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
     "vmat_set_master_method": [_p, _i32],
     "vmat_set_price_smoothing": [_p, _i32],
+    "vmat_set_master_precision": [_p, _i32],
     "vmat_dvh": [_p, _p, _d, _i32, _p],
     "vmat_dose_rate_feasibility": [_p, _d, _d, _i32, _i32, _d, _p, _p, _p, _p, _p],
 }
@@ -193,6 +194,7 @@ def vmat_get_info(ctx) -> dict:
     _check(ctx, load_library().vmat_get_info(ctx, ctypes.byref(inf)))
     out = {k: getattr(inf, k) for k, _ in vmat_info._fields_}
     out["master_ms"] = list(out["master_ms"])
+    out["tile_entries"] = list(out["tile_entries"])
     return out
 
 
@@ -412,6 +414,9 @@ class Plan:
         """'pg' (the paper's gradient projection, default) or 'newton'."""
         vmat_set_master_method(self.ctx, method)
 
+    def set_master_precision(self, extended=True):
+        vmat_set_master_precision(self.ctx, extended)
+
     def set_price_smoothing(self, on=True):
         """Price beams by the exact reduced cost (beamlet sum + gamma dG/dy_k)
         instead of the beamlet sum alone (the default, as in the paper)."""
@@ -453,6 +458,10 @@ MASTER_METHODS = {"pg": VMAT_MASTER_PROJECTED_GRADIENT, "newton": VMAT_MASTER_PR
 
 def vmat_set_master_method(ctx, method):
     _check(ctx, load_library().vmat_set_master_method(ctx, int(MASTER_METHODS.get(method, method))))
+
+
+def vmat_set_master_precision(ctx, extended):
+    _check(ctx, load_library().vmat_set_master_precision(ctx, int(bool(extended))))
 
 
 def vmat_set_price_smoothing(ctx, on):
