@@ -62,14 +62,14 @@ def lib():
             "vo_leaf_limits": (None, [_c_i32] * 5 + [_p, _p, _p, _c_i32, _p, _p, _p, _p]),
             "vo_row_scan": (_c_i32, [_c_i32, _p, _c_i32, _c_i32, _c_i32, _c_i32, _p, _p, _p]),
             "vo_row_scan_f32": (_c_i32, [_c_i32, _p, _c_i32, _c_i32, _c_i32, _c_i32, _p, _p, _p]),
-            "vo_pricing": (_c_i32, [_c_i32] * 5 + [_p, _p, _p, _p, _c_i32, _p, _p, _p, _p, _p, _p, _p]),
+            "vo_pricing": (_c_i32, [_c_i32] * 5 + [_p, _p, _p, _p, _c_i32, _p, _p, _p, _p, _p, _p, _p, _p]),
             "vo_line_search": (_c_d, [_c_i64, _p, _p, _p, _p, _p, _p, _c_d, _c_d, _c_d]),
             "vo_master": (_c_i32, [_c_i64, _c_i32, _p, _p, _c_i32, _p, _c_i32, _c_d, _p, _p, _p,
                                    _p, _c_d, _c_d, _c_i32, _p, _p, _p]),
             "vo_dvh": (None, [_c_i64, _p, _p, _c_i32, _c_d, _c_i32, _p]),
             "vo_colgen": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32, _p, _p, _p, _p, _p, _p, _p,
                                    _p, _c_d, _c_i32, _c_i32, _c_i32, _c_d, _c_i32, _p, _p, _p,
-                                   _c_i32, _c_i32] + [_p] * 12),
+                                   _c_i32, _c_i32] + [_p] * 14),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -215,15 +215,17 @@ def pricing(cfg, occ, lleaf, rleaf, g, f32=False, N=None, R=None, C=None, s=None
     p = ctypes.c_double()
     p2 = ctypes.c_double()
     rm = ctypes.c_double()
+    res = np.zeros(2)
     off = None if offset is None else _f64(offset)
     if off is not None and off.size != N:
         raise ValueError("offset must have one value per beam")
     rc = lib().vo_pricing(N, R, C, s, int(cyclic), _ptr(occ), _ptr(lleaf), _ptr(rleaf), _ptr(g),
                           int(f32), ctypes.byref(k), _ptr(lo), _ptr(ro), ctypes.byref(p),
-                          ctypes.byref(p2), ctypes.byref(rm), _ptr(off))
+                          ctypes.byref(p2), ctypes.byref(rm), _ptr(off), _ptr(res))
     if rc != 0:
         raise RuntimeError(f"oracle pricing failed: {rc}")
-    return dict(k=k.value, l=lo, r=ro, p=p.value, p2=p2.value, row_margin=rm.value)
+    return dict(k=k.value, l=lo, r=ro, p=p.value, p2=p2.value, row_margin=rm.value,
+                f32_res=res[0], row_res=res[1])
 
 
 def smoothing_offset(theta, y, gamma, cyclic=True) -> np.ndarray:
@@ -273,7 +275,8 @@ def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricin
     n_iter = cfg.iterations if n_iter is None else n_iter
     eps = cfg.kkt_eps if eps is None else eps
     rec = dict(k=np.zeros(n_iter, np.int32), p=np.zeros(n_iter), margin=np.zeros(n_iter),
-               row_margin=np.zeros(n_iter), cost=np.zeros(n_iter), rho=np.zeros(n_iter),
+               row_margin=np.zeros(n_iter), f32_res=np.zeros(n_iter), row_res=np.zeros(n_iter),
+               cost=np.zeros(n_iter), rho=np.zeros(n_iter),
                iters=np.zeros(n_iter, np.int32), status=np.zeros(n_iter, np.int32))
     y = np.zeros(N)
     z = np.zeros(prob.n_vox)
@@ -290,7 +293,7 @@ def colgen(prob, n_iter=None, eps=None, max_iter=100000, forced=None, f32_pricin
         _ptr(prob.struct_id), _ptr(T), _ptr(alpha), _ptr(beta), _ptr(theta), cfg.gamma,
         int(cfg.cyclic), cfg.max_leaf_step, n_iter, eps, max_iter, _ptr(fk), _ptr(fl), _ptr(fr),
         int(f32_pricing), int(price_smoothing), _ptr(rec["k"]), _ptr(rec["p"]), _ptr(rec["margin"]),
-        _ptr(rec["row_margin"]), _ptr(rec["cost"]), _ptr(rec["rho"]), _ptr(rec["iters"]),
+        _ptr(rec["row_margin"]), _ptr(rec["f32_res"]), _ptr(rec["row_res"]), _ptr(rec["cost"]), _ptr(rec["rho"]), _ptr(rec["iters"]),
         _ptr(rec["status"]), _ptr(y), _ptr(z), _ptr(lleaf), _ptr(rleaf))
     if rc != 0:
         raise RuntimeError(f"oracle colgen failed: {rc}")

@@ -266,15 +266,37 @@ static double row_runner_up(int C, const double *g, int Llo, int Lhi, int Rlo, i
  * offset [N] (NULL: none) is added to each beam's price after the row sum:
  * the column generation passes gamma * dG/dy_k of Eq. 2 at the current y for
  * the exact reduced cost of a new column (see vo_colgen).
+ * res [2] (NULL to skip): the resolution of the decision when the row scans
+ * run in single precision.  A row value P[r] - P[l] is a difference of
+ * prefix sums, so one unit in the last place of the row's largest prefix sum
+ * |P| (2^-23 of it) is the least change a one-ulp change of a single price
+ * can make to it.  res[0] = 2^-23 times the sum over the rows of the chosen
+ * beam and of the runner-up beam of their largest |P| (an absolute price);
+ * res[1] = the least, over the rows of the chosen beam, of the row's margin
+ * (runner-up value minus chosen value, FP64) over 2^-22 times its largest |P|.
  * Returns 0, -1 if no beam is free, -2 if some free beam has an infeasible row. */
+/* sum over the rows of beam k of the largest |prefix sum| of the row */
+static double beam_prefix_scale(int R, int C, const double *gk) {
+  double sum = 0.0;
+  for (int rr = 0; rr < R; ++rr) {
+    double P = 0.0, mx = 0.0;
+    for (int c = 0; c < C; ++c) {
+      P += gk[(int64_t)rr * C + c];
+      if (fabs(P) > mx) mx = fabs(P);
+    }
+    sum += mx;
+  }
+  return sum;
+}
+
 int vo_pricing(int N, int R, int C, int s, int cyclic, const uint8_t *occ, const int16_t *lleaf,
                const int16_t *rleaf, const double *g, int f32, int *kstar, int16_t *lout,
                int16_t *rout, double *pstar, double *p2, double *row_margin,
-               const double *offset) {
+               const double *offset, double *res) {
   int *Llo = malloc(sizeof(int) * R * 4);
   int *Lhi = Llo + R, *Rlo = Llo + 2 * R, *Rhi = Llo + 3 * R;
   float *gf = malloc(sizeof(float) * C);
-  int best = -1, status = 0;
+  int best = -1, ksecond = -1, status = 0;
   double bp = 0.0, second = INFINITY;
   for (int k = 0; k < N; ++k) {
     if (occ[k]) continue;
@@ -297,15 +319,16 @@ int vo_pricing(int N, int R, int C, int s, int cyclic, const uint8_t *occ, const
     }
     if (offset) p += offset[k];
     if (best < 0 || p < bp) {
-      if (best >= 0) second = bp;
+      if (best >= 0) { second = bp; ksecond = best; }
       best = k; bp = p;
     } else if (p < second) {
       second = p;
+      ksecond = k;
     }
   }
   if (best < 0) { status = -1; goto done; }
   vo_leaf_limits(N, R, C, s, cyclic, occ, lleaf, rleaf, best, Llo, Lhi, Rlo, Rhi);
-  double margin = INFINITY;
+  double margin = INFINITY, row_res = INFINITY;
   for (int rr = 0; rr < R; ++rr) {
     const double *grow = g + ((int64_t)best * R + rr) * C;
     int l, r;
@@ -319,15 +342,24 @@ int vo_pricing(int N, int R, int C, int s, int cyclic, const uint8_t *occ, const
       vo_row_scan(C, grow, Llo[rr], Lhi[rr], Rlo[rr], Rhi[rr], &v, &l, &r);
     }
     lout[rr] = (int16_t)l; rout[rr] = (int16_t)r;
-    if (row_margin) {
+    if (row_margin || res) {
       double vx = 0.0; /* chosen interval's value in FP64 */
       for (int c = l; c < r; ++c) vx += grow[c];
       double ru = row_runner_up(C, grow, Llo[rr], Lhi[rr], Rlo[rr], Rhi[rr], vx);
       if (ru - vx < margin) margin = ru - vx;
+      double unit = 0x1p-22 * beam_prefix_scale(1, C, grow);
+      double q = unit > 0.0 ? (ru - vx) / unit : INFINITY;
+      if (q < row_res) row_res = q;
     }
   }
   *kstar = best; *pstar = bp; *p2 = second;
   if (row_margin) *row_margin = margin;
+  if (res) {
+    double sc = beam_prefix_scale(R, C, g + (int64_t)best * R * C);
+    if (ksecond >= 0) sc += beam_prefix_scale(R, C, g + (int64_t)ksecond * R * C);
+    res[0] = 0x1p-23 * sc;
+    res[1] = row_res;
+  }
 done:
   free(Llo);
   free(gf);
@@ -549,8 +581,10 @@ int vo_master(int64_t V, int ncol, const double *M, const int32_t *col_beam, int
  * master.  If forced_k is non-NULL iteration t takes beam forced_k[t] with
  * leaves forced_l/forced_r [n_iter*R] instead of the pricing result (replay).
  * Per-iteration records (arrays of n_iter): beam, p*, angle margin
- * (p2-p*)/max(|p*|,1e-300), least row margin / max(|p*|,1e-300), cost,
- * rho, master iterations, master status.  The master problems stop at
+ * (p2-p*)/max(|p*|,1e-300), least row margin / max(|p*|,1e-300), the
+ * single-precision resolution of the beam decision / max(|p*|,1e-300) and
+ * the least row margin in units of its row's resolution (see vo_pricing;
+ * either record may be NULL), cost, rho, master iterations, master status.  The master problems stop at
  * rho <= eps * max(rho_start, rho_plan), rho_plan = the residual at the start
  * of the first one.  Final y [N], z [V], leaves
  * lleaf/rleaf [N*R] (rows of beams without an aperture are 0).
@@ -567,6 +601,7 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
               int n_iter, double eps, int max_iter, const int32_t *forced_k,
               const int16_t *forced_l, const int16_t *forced_r, int f32_pricing,
               int price_smoothing, int32_t *rec_k, double *rec_p, double *rec_margin, double *rec_row_margin,
+              double *rec_res, double *rec_row_res,
               double *rec_cost, double *rec_rho, int32_t *rec_iters, int32_t *rec_status,
               double *y, double *z, int16_t *lleaf, int16_t *rleaf) {
   const int64_t B = (int64_t)N * R * C;
@@ -592,13 +627,16 @@ int vo_colgen(int64_t V, int N, int R, int C, const int64_t *row_ptr, const int3
       vo_dG(N, theta, y, cyclic, off);
       for (int q = 0; q < N; ++q) off[q] *= gamma;
     }
+    double res[2];
     int rc = vo_pricing(N, R, C, s, cyclic, occ, lleaf, rleaf, g, f32_pricing, &k, lk, rk, &p,
-                        &p2, &rm, price_smoothing ? off : NULL);
+                        &p2, &rm, price_smoothing ? off : NULL, res);
     if (rc != 0) { status = rc; break; }
     double scale = fabs(p) > 1e-300 ? fabs(p) : 1e-300;
     rec_p[t] = p;
     rec_margin[t] = (p2 - p) / scale;
     rec_row_margin[t] = rm / scale;
+    if (rec_res) rec_res[t] = res[0] / scale;
+    if (rec_row_res) rec_row_res[t] = res[1];
     if (forced_k) {
       k = forced_k[t];
       memcpy(lk, forced_l + (int64_t)t * R, sizeof(int16_t) * R);

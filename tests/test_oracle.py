@@ -375,3 +375,19 @@ def test_colgen_replay_reproduces_itself(small_problem):
     rep = oracle.colgen(p, eps=1e-8, forced=(rec["k"], fl, fr))
     assert np.array_equal(rep["k"], rec["k"])
     np.testing.assert_array_equal(rep["cost"], rec["cost"])
+
+
+def test_pricing_single_precision_resolution_by_hand():
+    """One free beam with one row g = [1, -2, -1, 3, -4] (prefix sums 1, -1,
+    -2, 1, -3, largest |P| = 3): the resolution of the beam decision is one
+    unit in the last place of 3 in single precision, 2^-23 * 3 (no runner-up
+    beam); the row's chosen interval [4, 5) has value -4 and the least value
+    strictly above it is -3 ([1, 3)), so its margin is 1, i.e.
+    1 / (2^-22 * 3) units of the row's resolution."""
+    cfg = inputs.small_config(n_angles=1, n_rows=1, n_cols=5, max_leaf_step=5)
+    g = np.array(GOLD["row_scan"]["g"], dtype=np.float64)
+    out = oracle.pricing(cfg, np.zeros(1, np.uint8), np.zeros(1, np.int16), np.zeros(1, np.int16),
+                         g, f32=True)
+    assert (out["k"], int(out["l"][0]), int(out["r"][0])) == (0, 4, 5)
+    assert out["f32_res"] == 2.0 ** -23 * 3
+    assert out["row_res"] == pytest.approx(1.0 / (2.0 ** -22 * 3), rel=1e-15)
