@@ -41,14 +41,14 @@ def test_batched_plans_vs_oracle(asym_problems):
     takes the oracle's decisions wherever they are not near-ties, with its
     costs within 1e-5."""
     refs = [dec.oracle_plan(p) for p in asym_problems]
-    plans = [vmat.Plan(p) for p in asym_problems]
+    plans = [dec.precise(vmat.Plan(p)) for p in asym_problems]
     try:
         with vmat.Batch(plans) as batch:
             batch.configure(2)
             outs, _, _ = batch.run(kkt_tol=dec.GPU_KKT)
         for prob, ref, out in zip(asym_problems, refs, outs):
             n = prob.cfg.iterations
-            first_tie = next((t for t in range(n) if dec.margin(ref, t) <= dec.NEAR_TIE), n)
+            first_tie = next((t for t in range(n) if dec.near_tie(ref, t)), n)
             agree = dec.check_unforced(out, ref, prob.cfg.n_rows)
             assert agree >= first_tie and agree >= n - 2, (prob.cfg.name, agree, first_tie, n)
     finally:

@@ -47,6 +47,7 @@ def test_degenerate_plans(case, method):
     ref = dec.oracle_plan(prob)
     with vmat.Plan(prob) as plan:
         plan.set_master_method(method)
+        dec.precise(plan)
         gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
         assert sorted(gpu["k"].tolist()) == list(range(cfg.n_angles))
         assert np.all(gpu["y"] >= 0)
@@ -66,6 +67,7 @@ def test_largest_beam_count():
         with pytest.raises(vmat.VmatError) as e:
             plan.set_master_method("newton")
         assert e.value.status == vmat.VMAT_EINVAL
+        dec.precise(plan)
         gpu = plan.colgen_run(n_iters=24, kkt_tol=dec.GPU_KKT)
         dec.check_unforced(gpu, ref, prob.cfg.n_rows)
         plan.reset()

@@ -139,12 +139,16 @@ def test_prostate_first_iterations(prostate, pplan):
     R, n = cfg.n_rows, 20
     ref = dec.oracle_plan(prostate, n_iter=n)
     pplan.reset()
-    gpu = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT)
-    dec.check_unforced(gpu, ref, R)
-    pplan.reset()
-    rep = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
-    dec.check_replay(rep, ref, R)
-    pplan.reset()
+    dec.precise(pplan)
+    try:
+        gpu = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT)
+        dec.check_unforced(gpu, ref, R)
+        pplan.reset()
+        rep = pplan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
+        dec.check_replay(rep, ref, R)
+    finally:
+        pplan.reset()
+        pplan.set_master_precision(False)
 
 
 def test_prostate_off_centre_decisions():
@@ -159,8 +163,9 @@ def test_prostate_off_centre_decisions():
     prob = inputs.make_problem(cfg)
     R, n = cfg.n_rows, 24
     ref = dec.oracle_plan(prob, n_iter=n)
-    first_tie = next((t for t in range(n) if dec.margin(ref, t) <= dec.NEAR_TIE), n)
+    first_tie = next((t for t in range(n) if dec.near_tie(ref, t)), n)
     with vmat.Plan(prob, val_f32=True) as plan:
+        dec.precise(plan)
         gpu = plan.colgen_run(n_iters=n, kkt_tol=dec.GPU_KKT)
         assert dec.check_unforced(gpu, ref, R) >= first_tie
         plan.reset()

@@ -48,12 +48,14 @@ def test_newton_master_reaches_the_oracle_optimum(tiny, n_cols):
     M = np.array([oracle.aperture_dose(tiny, k, ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
                   for k in order])
     ref = oracle.master(M, np.array(order), tiny.theta_deg, tiny.struct_id, tiny.T, tiny.alpha,
-                        tiny.beta, cfg.gamma, cfg.cyclic, np.zeros(cfg.n_angles), eps=1e-11)
+                        tiny.beta, cfg.gamma, cfg.cyclic, np.zeros(cfg.n_angles),
+                        eps=dec.ORACLE_EPS)
     assert ref["status"] == 0
     iters = {}
     for method in ("pg", "newton"):
         with vmat.Plan(tiny) as plan:
             plan.set_master_method(method)
+            dec.precise(plan)
             for k in order:
                 plan.add_column(k, ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
             y = np.zeros(cfg.n_angles)
@@ -74,6 +76,7 @@ def test_newton_column_generation_tiny(tiny):
     ref = dec.oracle_plan(tiny)
     with vmat.Plan(tiny) as plan:
         plan.set_master_method("newton")
+        dec.precise(plan)
         gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
         dec.check_unforced(gpu, ref, R)
         # the oracle's plan replayed: decisions where they are not near-ties,

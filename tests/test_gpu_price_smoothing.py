@@ -91,6 +91,7 @@ def test_colgen_with_smoothing(cyclic, method):
     assert np.any(ref["k"] != lit["k"])  # a case where the option matters
     with vmat.Plan(prob) as plan:
         plan.set_master_method(method)
+        dec.precise(plan)
         plan.set_price_smoothing(True)
         gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
         first = dec.check_unforced(gpu, ref, R)
@@ -117,6 +118,7 @@ def test_tiny_plan_with_smoothing():
     R = cfg.n_rows
     ref = dec.oracle_plan(prob, price_smoothing=True)
     with vmat.Plan(prob) as plan:
+        dec.precise(plan)
         plan.set_price_smoothing(True)
         gpu = plan.colgen_run(kkt_tol=dec.GPU_KKT)
         dec.check_unforced(gpu, ref, R)
