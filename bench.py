@@ -36,10 +36,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
-# current kernel (bench.py --case master: 8.083971 GB read + 6.172 MB written
-# for (2*30+1) passes x 150 columns x 221,440 voxels x 4 B + z, F' out); set
-# to None whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (8.083971e9 + 6.172160e6) / ((2 * 30 + 1) * 150 * 221440 * 4 + 8 * 221440)
+# current kernel on the plan's own apertures (bench.py --case master-plan
+# --case-cols 90: 68.381952 MB read + 0.980992 MB written against 3,987,974,144
+# algorithmic bytes of that launch); set to None whenever the kernel changes
+# until it has been captured again
+MASTER_TRAFFIC_RATIO = (68.381952e6 + 0.980992e6) / 3987974144
+# L2 sector peak of that capture: 151.537635 sectors/ns at 13.936238% of peak
+# sustained elapsed, 32 B per sector
+L2_PEAK_GBS = 151.537635 / 0.13936238 * 32
 UNIT = "CG iters/s"
 
 
@@ -301,19 +305,24 @@ def run_ours(args):
         "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4) if dom_gbs else None,
         "peak_kind": f"{peak_kind} copy bandwidth",
         # DRAM bytes per launch = measured traffic/algorithmic ratio of one ncu capture of
-        # this kernel (half-depth phantom, 150 columns, 30 iterations) times this launch's
-        # algorithmic bytes
+        # this kernel on a plan's own apertures (half-depth phantom, 90 columns, 30
+        # iterations) times this launch's algorithmic bytes
         "traffic": (round(MASTER_TRAFFIC_RATIO * float(mb.sum()) / n_master, 0)
                     if dom == 3 and MASTER_TRAFFIC_RATIO else None),
-        "traffic_note": "per launch (average over the plan), scaled from one ncu capture of a "
-                        "smaller case; see profiles/k_master_halfdepth_150cols.md",
+        "traffic_note": "per launch (average over the plan), scaled from one ncu capture of the "
+                        "same kernel on a half-depth prostate plan's own 90 apertures (65 MB of "
+                        "nonzero column subtiles, L2-resident): DRAM/algorithmic = 0.0174",
+        "l2": ({"achieved": round(dom_gbs, 1), "peak": round(L2_PEAK_GBS, 1), "unit": "GB/s",
+                "frac": round(dom_gbs / L2_PEAK_GBS, 4),
+                "peak_kind": "L2 sector peak of the ncu capture (34.8 TB/s)"} if dom == 3 else None),
         "launches_per_step": n_master,
         "bytes_per_step": float(mb.sum()),
-        "dense_column_equivalent_GB/s": round(db.sum() / (ph_tot[3] / 1e3) / 1e9, 1),
         "note": ("master algorithmic bytes per launch = (2*P+1) reads of the nonzero subtiles "
                  "of the plan's aperture-dose columns (4 B per voxel) + z and F' written; "
-                 "P = projected-gradient iterations of the launch; while the nonzero part "
-                 "of the columns fits in L2 (126 MB) part of it is served from L2"),
+                 "P = projected-gradient iterations of the launch; the nonzero part of the "
+                 "columns fits in L2 (126 MB) and is read from DRAM about once per launch, so "
+                 "frac (HBM) is not this kernel's bound: it is latency- and barrier-bound "
+                 "(l2.frac, and the ncu stall counters)"),
     }
     # stand-alone SpMV bandwidth of the two sparse products at full D (FP32)
     x = torch.rand(prob.n_beamlets, device="cuda")
@@ -371,8 +380,18 @@ def run_ours(args):
         if args.master == "pg":
             out["projected_newton"] = run_newton(prob, plan, recs[-1], kkt, args)
         out["e2e"] = run_e2e(prob, args)
-        out["cpu_baseline"] = run_cpu_baseline(prob, args)
     plan.close()
+    if rank == 0 and ws == 1 and not args.quick:
+        extra = {}
+        if args.workload == "prostate" and not args.headline_only:
+            hn = inputs.make_problem(inputs.headneck_config())
+            out["headneck"] = run_workload_leg(hn, args)
+            extra["headneck"] = hn
+            out["batched"] = run_batched_leg(args)
+        out["cpu_baseline"] = run_cpu_baseline(prob, args, extra)
+        out["headline"] = ("value, roofline, e2e and cpu_baseline.value: the prostate workload "
+                           "(config.workload); headneck and batched are further workloads in the "
+                           "same run")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -569,6 +588,42 @@ def run_variants(prob, plan32, rec32, kkt=1e-6):
     return res
 
 
+def run_workload_leg(prob, args):
+    """Another single-plan workload in the default run: one plan per storage
+    type of D (FP32, FP16, BF16 with per-beamlet scale), each timed over
+    --steps plans after one warm-up, with the plan's own GPU dose against the
+    FP64 NumPy dose of its apertures and intensities."""
+    import torch
+    from paper_1005_4396_b300 import vmat
+    cfg = prob.cfg
+    kkt = max(cfg.kkt_eps, 1e-6)
+    res = {"workload": _describe(cfg, prob)}
+    for dt in ("f32", "f16", "bf16"):
+        with vmat.Plan(prob, dtype=dt, val_f32=True) as p:
+            p.reset()
+            p.colgen_run(kkt_tol=kkt)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(args.steps):
+                p.reset()
+                r = p.colgen_run(kkt_tol=kkt)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / args.steps
+            z = p.plan_dose().cpu().numpy()
+            emax, emean = _dose_err(prob, p, z, r["lleaf"], r["rleaf"], r["y"])
+            res[dt] = {"cg_iters_per_s": round(len(r["k"]) / t, 3), "s_per_plan": round(t, 4),
+                       "master_iters": int(r["iters"].sum()),
+                       "max_dose_err_pct_rx": round(emax, 5), "mean_dose_err_pct_rx": round(emean, 6),
+                       "within_0.5pct": bool(emax <= 0.5), "final_cost": float(r["cost"][-1]),
+                       "device_bytes": p.info["device_bytes"]}
+    res["note"] = ("CUDA events around --steps whole plans (D resident); dose error: the plan's "
+                   "own GPU dose against the FP64 dose of the same apertures and intensities, "
+                   "% of the largest prescription")
+    return res
+
+
 def run_e2e(prob, args):
     """Same metric through the C-ABI from pinned host buffers: create (H2D of
     D and the problem), one plan, read back the result, destroy."""
@@ -623,28 +678,99 @@ def _oracle_sample(prob, n_iter):
     return time.perf_counter() - t0, rec
 
 
-def run_cpu_baseline(prob, args):
+def _omp_threads(n):
+    """Thread count of the oracle's OpenMP regions started from this thread."""
+    import ctypes.util
+    name = ctypes.util.find_library("gomp") or "libgomp.so.1"
+    ctypes.CDLL(name).omp_set_num_threads(int(n))
+
+
+def _oracle_operator_rates(prob, seed=5, n_master_cols=None, master_iters=3):
+    """Per-operator rates of the FP64 oracle on one workload: dose z = D^T x,
+    price g = D F'(z), and one projected-gradient master iteration with half
+    the beams holding a seeded deliverable aperture."""
     import oracle
+    from paper_1005_4396_b300 import inputs
+    cfg = prob.cfg
+    x = inputs.rng.uniform(seed, prob.n_beamlets)
+    t0 = time.perf_counter()
+    z = oracle.dose(prob, x)
+    t_dose = time.perf_counter() - t0
+    f = oracle.voxel_dcost(z, prob.struct_id, prob.T, prob.alpha, prob.beta)
+    t0 = time.perf_counter()
+    oracle.price(prob, f)
+    t_price = time.perf_counter() - t0
+    R = cfg.n_rows
+    ll, rr = inputs.random_apertures(seed, cfg)
+    ncol = n_master_cols or cfg.n_angles // 2
+    beams = np.arange(0, cfg.n_angles, max(1, cfg.n_angles // ncol))[:ncol]
+    M = np.array([oracle.aperture_dose(prob, k, ll[k * R:(k + 1) * R], rr[k * R:(k + 1) * R])
+                  for k in beams])
+    y0 = np.zeros(cfg.n_angles)
+    t0 = time.perf_counter()
+    res = oracle.master(M, beams, prob.theta_deg, prob.struct_id, prob.T, prob.alpha, prob.beta,
+                        cfg.gamma, cfg.cyclic, y0, eps=0.0, max_iter=master_iters)
+    t_master = (time.perf_counter() - t0) / max(res["iters"], 1)
+    return {"dose_per_s": round(1 / t_dose, 4), "price_per_s": round(1 / t_price, 4),
+            "master_iter_per_s": round(1 / t_master, 4), "master_columns": int(ncol)}
+
+
+def run_cpu_baseline(prob, args, extra=None):
+    """The FP64 oracle on the host cores: the headline sample (first
+    --cpu-iters iterations of the timed plan, all threads), then per-operator
+    rates at all threads and at one thread on this workload (and on any
+    `extra` workloads), and the whole tiny plan at both thread counts."""
+    import oracle
+    from paper_1005_4396_b300 import inputs
     oracle.build()
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    _omp_threads(cores)
     n = args.cpu_iters
     dt, _ = _oracle_sample(prob, n)
-    return {"value": round(n / dt, 4), "unit": UNIT, "cores": int(cores), "kind": "oracle",
-            "sample": f"first {n} column-generation iterations of the same plan (FP64 oracle, "
-                      f"OpenMP over {cores} threads, {dt:.1f} s); early iterations have the "
-                      f"fewest columns, so this overstates the oracle's whole-plan rate"}
+    out = {"value": round(n / dt, 4), "unit": UNIT, "cores": int(cores), "kind": "oracle",
+           "sample": f"first {n} column-generation iterations of the same plan (FP64 oracle, "
+                     f"OpenMP over {cores} threads, {dt:.1f} s); early iterations have the "
+                     f"fewest columns, so this overstates the oracle's whole-plan rate"}
+    if args.quick:
+        return out
+    tiny = inputs.make_problem(inputs.tiny_config())
+    rates = {}
+    for threads in (cores, 1):
+        _omp_threads(threads)
+        key = f"threads_{threads}"
+        rates[key] = {}
+        t0 = time.perf_counter()
+        oracle.colgen(tiny)
+        rates[key]["tiny_whole_plan"] = {"s": round(time.perf_counter() - t0, 3),
+                                         "cg_iters_per_s": round(tiny.cfg.iterations / (time.perf_counter() - t0), 3)}
+        for name, p in [(prob.cfg.name, prob)] + list((extra or {}).items()):
+            rates[key][name] = _oracle_operator_rates(p)
+    _omp_threads(cores)
+    out["operator_rates"] = rates
+    out["operator_note"] = ("dose: z = D^T x (serial scatter, the same at every thread count); price: "
+                            "g = D F'(z) over all beamlets; master: one projected-gradient iteration "
+                            "(two FP64 passes over the columns + exact line search) with half the beams "
+                            "holding an aperture; tiny_whole_plan: 36 iterations at KKT 1e-8")
+    return out
 
 
 # ---------------------------------------------------------------- batched plans
 def run_batched(args):
+    """The batched workload alone (see run_batched_leg), as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    out = run_batched_leg(args)
+    print(json.dumps(out), flush=True)
+
+
+def run_batched_leg(args):
     """Sixteen independent plans of uneven size (seeds 10-25: 90-180 beams,
     40x40 or 60x40 MLC, prostate- or head-and-neck-like, 0.4-2.2 M voxels):
     FP16-D plans in one tuned batch (per-plan SM budgets, plans side by side, one CUDA graph
     launch) against the plain FP32 single-plan loop on the same GPU."""
     import torch
     from paper_1005_4396_b300 import inputs, vmat
-    torch.cuda.set_device(0)
     cfgs = inputs.batch_configs(scale=args.batch_scale)
     kkt = 1e-6
     plans16, probs, fp32 = [], [], []
@@ -699,7 +825,7 @@ def run_batched(args):
     batch.close()
     for p in plans16:
         p.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_autograd(args):
@@ -756,6 +882,22 @@ def run_autograd(args):
             ms = a.elapsed_time(b) / args.steps
             out[name] = {"ms_per_call": round(ms, 3), "vectors_per_s": round(32 / (ms / 1e3), 1)}
         out["value"] = out["fluence"]["vectors_per_s"]
+        # roofline of the fluence call (dose forward + price backward on row tiles):
+        # algorithmic bytes = both tiled forms of D once (4 B index + 8 x 4 B values per
+        # union entry) + X read + Z and F' written + F' gathered onto active voxels + G
+        # written, 128 B per row each
+        info = vmat.vmat_get_info(plan.ctx)
+        te = info["tile_entries"]
+        Va, B, V = info["n_active"], prob.n_beamlets, prob.n_vox
+        byts = (te[0] + te[1]) * (4 + 8 * 4) + 128 * (B + 2 * V + 2 * Va + B)
+        gbs = byts / (out["fluence"]["ms_per_call"] / 1e3) / 1e9
+        peak, peak_kind = _peaks()
+        out["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(gbs / peak, 4), "peak_kind": f"{peak_kind} copy bandwidth",
+                           "bytes_per_call": int(byts), "tile_entries": te,
+                           "csr_nnz": prob.nnz,
+                           "note": "one fluence call: dose forward and price backward on row tiles of D "
+                                   "(8 rows per tile); the gathers of X and F' rows are L2 traffic"}
         # errors on sampled vectors
         step_x()
         gx = X.grad.cpu().numpy()
@@ -847,6 +989,27 @@ def run_case(args):
         y = np.zeros(cfg.n_angles)
         res = plan.master_step(max_iters=30, kkt_tol=1e-9, y=y)
         out.update(columns=int(args.case_cols), master=res)
+    elif args.case == "master-plan":
+        # the plan's own apertures: --case-cols column-generation iterations
+        # (one master launch each), then one more master launch of exactly 30
+        # projected-gradient iterations from the plan's y (tolerance 0 never
+        # stops early); its working set is that of the plan's hard masters
+        rec = plan.colgen_run(n_iters=args.case_cols, kkt_tol=1e-6)
+        res = plan.master_step(max_iters=30, kkt_tol=0.0)
+        info = plan.info
+        sub = int(rec["col_subtiles"].sum())
+        alg = (2 * 30 + 1) * sub * info["subtile_voxels"] * 4 + 8 * info["n_active"]
+        out.update(columns=int(args.case_cols), master=res, nonzero_subtiles=sub,
+                   nonzero_column_MB=round(sub * info["subtile_voxels"] * 4 / 1e6, 2),
+                   algorithmic_bytes_last_launch=alg, master_launch=[info["master_grid"], info["master_block"]])
+    elif args.case == "spmm32":
+        # the differentiable forward's batched products: 32 fluence vectors
+        X = torch.rand(prob.n_beamlets, 32, device="cuda")
+        for _ in range(2):
+            Z, Fp, _ = plan.dose_batch32(X)
+            plan.price_batch32(Fp)
+        torch.cuda.synchronize()
+        out.update(n_beamlets=prob.n_beamlets)
     else:
         x = torch.rand(prob.n_beamlets, device="cuda")
         f = torch.randn(prob.n_vox, device="cuda")
@@ -900,7 +1063,9 @@ def main():
     ap.add_argument("--workload", default="prostate", choices=["prostate", "tiny", "headneck"])
     ap.add_argument("--cpu-iters", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
-    ap.add_argument("--case", default=None, choices=["master", "spmv"],
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the head-and-neck and batched workloads of the default run")
+    ap.add_argument("--case", default=None, choices=["master", "master-plan", "spmv", "spmm32"],
                     help="small case for an ncu capture instead of the benchmark")
     ap.add_argument("--case-cols", type=int, default=150,
                     help="columns of the --case master launch (150: ~133 MB, above L2)")
