@@ -362,12 +362,11 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Stages of the direction pass's copy pipeline: column segments in flight per thread
-#ifndef MASTER_PASS_A_UNROLL
-#define MASTER_PASS_A_UNROLL 16
+// float4 loads of a lane's share of a (column, subtile) pair in the gradient
+// pass of a 512-thread CTA (threads / 32)
+#ifndef MASTER_PASS_A_LOADS
+#define MASTER_PASS_A_LOADS 16
 #endif
-// loads of the gradient pass in flight per lane (16: a 512-thread subtile's
-// whole share of a column; measured 4% faster gradient pass than 8)
-constexpr int master_pass_a_unroll = MASTER_PASS_A_UNROLL;
 __host__ __device__ constexpr int master_pipe_stages(int vpt) { return vpt >= 16 ? 8 : 16; }
 
 // Floats of the region holding the line-search rows ([nthr][33]); the
@@ -664,8 +663,22 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           dot2_add(acc, accc, q.w, f.w, fl.w);
           accc = fmaf(ql.x, f.x, fmaf(ql.y, f.y, fmaf(ql.z, f.z, fmaf(ql.w, f.w, accc))));
         }
+      } else if (lane4 == MASTER_PASS_A_LOADS) {
+        // 512-thread CTAs: the lane's whole share of the pair (16 float4)
+        // in flight at once (a runtime trip count below the unroll factor
+        // would run the loads one at a time, so other CTA sizes take the
+        // loop below)
+#pragma unroll
+        for (int i = 0; i < MASTER_PASS_A_LOADS; ++i) {
+          const float4 q = __ldg(Ms + lane + 32 * i);
+          const float4 f = F4[lane + 32 * i];
+          dot2_add1(acc, accc, q.x, f.x);
+          dot2_add1(acc, accc, q.y, f.y);
+          dot2_add1(acc, accc, q.z, f.z);
+          dot2_add1(acc, accc, q.w, f.w);
+        }
       } else {
-#pragma unroll master_pass_a_unroll
+#pragma unroll 8
         for (int i = 0; i < lane4; ++i) {
           const float4 q = __ldg(Ms + lane + 32 * i);
           const float4 f = F4[lane + 32 * i];
@@ -760,20 +773,6 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           s_g[4 * c4 + t] = (double)gs + (double)gc;  // M^T F'(z) of slot 4 c4 + t
         }
         __syncthreads();
-      }
-    }
-    // the direction pass's first copies (columns of the first own subtile)
-    // do not depend on the step: issue them now so they land during it (the
-    // projected-Newton step stages its Gram chunks in the same region)
-    if (!NEWTON) {
-      const int nm0 = s_mcnt[0];
-      const int *cl0 = s_mcols;
-      const float *src0 = a.M + SUB_OFF(0) + 4 * tid;
-      float4 *pipe0 = (float4 *)s_rows;
-#pragma unroll
-      for (int k = 0; k < master_pipe_stages(VPT); ++k) {
-        if (k < nm0) cp_async16(pipe0 + k * nthr + tid, src0 + (size_t)cl0[k] * a.Vpad);
-        cp_async_commit();
       }
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[0] += c1 - s_clk[4]; s_clk[4] = c1; }
@@ -1161,12 +1160,10 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         const int *cl = s_mcols + m * N;
         const float *src = a.M + SUB_OFF(m) + 4 * tid;
         float4 zz = make_float4(0.f, 0.f, 0.f, 0.f), ww = zz;
-        if (NEWTON || m > 0) {  // (the first subtile's copies went out before the step)
 #pragma unroll
-          for (int k = 0; k < STG; ++k) {
-            if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
-            cp_async_commit();
-          }
+        for (int k = 0; k < STG; ++k) {
+          if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
+          cp_async_commit();
         }
         if (refresh) {
           float4 zc4 = zz;
@@ -1392,7 +1389,6 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     __syncthreads();
   }
 
-  cp_async_wait<0>();  // a solve that stops in the step phase has direction-pass copies in flight
   if (!alive) {
     if (blockIdx.x == 0 && tid == 0) {
       a.out->status = VMAT_ETIMEOUT;

@@ -8,6 +8,8 @@ import pytest
 import oracle
 from paper_1005_4396_b300 import inputs
 
+import decisions as dec
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -22,13 +24,17 @@ def test_coarse_plan_parity_and_full_resolution_quality():
     fine = inputs.make_problem(cfg)
     cp = inputs.coarse_tissue(fine)
     R = cfg.n_rows
-    ref = oracle.colgen(cp.prob, eps=1e-8)
-    fl = np.array([ref["lleaf"][k * R:(k + 1) * R] for k in ref["k"]])
-    fr = np.array([ref["rleaf"][k * R:(k + 1) * R] for k in ref["k"]])
+    ref = dec.oracle_plan(cp.prob)
     with vmat.Plan(cp.prob) as plan:
-        rep = plan.colgen_run(kkt_tol=1e-6, forced=(ref["k"], fl, fr))
-        np.testing.assert_allclose(rep["cost"], ref["cost"], rtol=1e-5)
+        # the merged problem's decisions under the rule of tests/decisions.py
+        dec.precise(plan)
+        rep = plan.colgen_run(kkt_tol=dec.GPU_KKT, forced=dec.forced(ref, R))
+        dec.check_replay(rep, ref, R)
         plan.reset()
+        dec.check_unforced(plan.colgen_run(kkt_tol=dec.GPU_KKT), ref, R)
+        # the default master's own plan, evaluated at full resolution below
+        plan.reset()
+        plan.set_master_precision(False)
         gpu = plan.colgen_run(kkt_tol=1e-6)
     with vmat.Plan(fine) as fplan:
         x = oracle.aperture_fluence(cfg, gpu["lleaf"], gpu["rleaf"], gpu["y"])
