@@ -14,8 +14,9 @@
 // pass skip all-zero subtiles.  Per iteration:
 //   pass A   gradient M^T F'(z): F' of the CTA's subtiles goes to shared
 //            memory; each warp streams whole (column, subtile) pairs with
-//            many independent 16-byte loads per lane, compensated dot
-//            products per lane and a compensated warp sum
+//            many independent 16-byte loads per lane; per lane, the four
+//            products of each float4 are summed in FP32 and those block sums
+//            compensated; then a compensated warp sum
 //   reduce   per-slot CTA partials (FP32 rows) -> grid barrier -> every CTA
 //            sums all rows in the same fixed order, compensated (one barrier;
 //            deterministic, no float atomics)
@@ -193,15 +194,21 @@ __device__ __forceinline__ void dot2_add(float &s, float &c, float a, float bh, 
   c = __fadd_rn(c, __fmaf_rn(a, bl, __fadd_rn(e, pe)));
 }
 
-// s + c += a * b, compensated as dot2_add (b without a low part)
-__device__ __forceinline__ void dot2_add1(float &s, float &c, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float pe = __fmaf_rn(a, b, -p);
-  const float t = __fadd_rn(s, p);
+// s + c += q . f over a float4 (4 voxels of one column): the four products
+// summed by one FMA chain in FP32, and that block sum added to (s, c)
+// compensated (TwoSum).  The chain's few roundings, on four terms of
+// neighbouring voxels, are the only error kept; over the ~500 blocks of a
+// (column, subtile) pair they add up at random and stay below the rounding
+// of the pair's result to FP32.  11 FP32 operations per 4 products, against
+// 40 for products compensated one by one (TwoProduct and TwoSum each),
+// which left the gradient pass bound by instruction issue.
+__device__ __forceinline__ void dot4_add(float &s, float &c, const float4 &q, const float4 &f) {
+  const float b = __fmaf_rn(q.w, f.w, __fmaf_rn(q.z, f.z, __fmaf_rn(q.y, f.y, __fmul_rn(q.x, f.x))));
+  const float t = __fadd_rn(s, b);
   const float bp = __fsub_rn(t, s);
-  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(b, bp));
   s = t;
-  c = __fadd_rn(c, __fadd_rn(e, pe));
+  c = __fadd_rn(c, e);
 }
 
 // derivative of the smoothing term G (Eq. 2) at beam k, from inverse gaps
@@ -361,12 +368,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// One lane's share of a (column, subtile) pair in the gradient pass: all L
+// float4 loads of the column issued at once, then summed against F' in
+// shared memory
+template <int L>
+__device__ __forceinline__ void pair_dot(const float4 *Ms, const float4 *F4, int lane, float &acc,
+                                         float &accc) {
+  float4 q[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) q[i] = __ldg(Ms + lane + 32 * i);
+#pragma unroll
+  for (int i = 0; i < L; ++i) dot4_add(acc, accc, q[i], F4[lane + 32 * i]);
+}
+
 // Stages of the direction pass's copy pipeline: column segments in flight per thread
-// float4 loads of a lane's share of a (column, subtile) pair in the gradient
-// pass of a 512-thread CTA (threads / 32)
-#ifndef MASTER_PASS_A_LOADS
-#define MASTER_PASS_A_LOADS 16
-#endif
 __host__ __device__ constexpr int master_pipe_stages(int vpt) { return vpt >= 16 ? 8 : 16; }
 
 // Floats of the region holding the line-search rows ([nthr][33]); the
@@ -663,29 +678,22 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           dot2_add(acc, accc, q.w, f.w, fl.w);
           accc = fmaf(ql.x, f.x, fmaf(ql.y, f.y, fmaf(ql.z, f.z, fmaf(ql.w, f.w, accc))));
         }
-      } else if (lane4 == MASTER_PASS_A_LOADS) {
-        // 512-thread CTAs: the lane's whole share of the pair (16 float4)
-        // in flight at once (a runtime trip count below the unroll factor
-        // would run the loads one at a time, so other CTA sizes take the
-        // loop below)
-#pragma unroll
-        for (int i = 0; i < MASTER_PASS_A_LOADS; ++i) {
-          const float4 q = __ldg(Ms + lane + 32 * i);
-          const float4 f = F4[lane + 32 * i];
-          dot2_add1(acc, accc, q.x, f.x);
-          dot2_add1(acc, accc, q.y, f.y);
-          dot2_add1(acc, accc, q.z, f.z);
-          dot2_add1(acc, accc, q.w, f.w);
-        }
       } else {
+        // the lane's whole share of the pair (lane4 = threads / 32 float4
+        // loads) in flight at once: a runtime trip count below a loop's
+        // unroll factor would issue the loads one at a time
+        switch (lane4) {
+#define PAIR_DOT_CASE(L) \
+  case L: pair_dot<L>(Ms, F4, lane, acc, accc); break;
+          PAIR_DOT_CASE(8) PAIR_DOT_CASE(9) PAIR_DOT_CASE(10) PAIR_DOT_CASE(11) PAIR_DOT_CASE(12)
+          PAIR_DOT_CASE(13) PAIR_DOT_CASE(14) PAIR_DOT_CASE(15) PAIR_DOT_CASE(16)
+#undef PAIR_DOT_CASE
+          default:
 #pragma unroll 8
-        for (int i = 0; i < lane4; ++i) {
-          const float4 q = __ldg(Ms + lane + 32 * i);
-          const float4 f = F4[lane + 32 * i];
-          dot2_add1(acc, accc, q.x, f.x);
-          dot2_add1(acc, accc, q.y, f.y);
-          dot2_add1(acc, accc, q.z, f.z);
-          dot2_add1(acc, accc, q.w, f.w);
+            for (int i = 0; i < lane4; ++i) {
+              const float4 q = __ldg(Ms + lane + 32 * i);
+              dot4_add(acc, accc, q, F4[lane + 32 * i]);
+            }
         }
       }
 #pragma unroll
@@ -1515,20 +1523,20 @@ static cudaError_t master_occupancy_any(int vpt, bool newton, bool xp, int nthr,
 }
 
 // Launch shape: the fewest voxels per thread (4, 8, 16, 32) that fit the
-// SMs with 512-thread CTAs, then threads per CTA chosen so that about
-// MASTER_CTA_TARGET CTAs cover the voxels, but never fewer than 256 threads
-// (small problems then take fewer CTAs: 8 warps per CTA hide the pass
-// latencies that 2-5 warps do not) and 512 from 16 voxels per thread on.  Fewer, larger CTAs make the grid
-// barriers and cross-CTA sums of every iteration cheaper; on B300 ~110 CTAs
-// still stream the columns at full bandwidth, while more voxels per thread
-// (16, 32) lengthen every per-voxel pass.
-#ifndef MASTER_CTA_TARGET
-#define MASTER_CTA_TARGET 112
-#endif
+// SMs with 512-thread CTAs, then threads per CTA chosen so that the CTAs
+// cover the voxels with one CTA on (nearly) every SM, but never fewer than
+// 256 threads (small problems then take fewer CTAs: 8 warps per CTA hide the
+// pass latencies that 2-5 warps do not) and 512 from 16 voxels per thread on.
+// The column passes are bound per SM (each warp's pairs in series, the
+// direction pass's copies and shared-memory traffic), so spreading the voxels
+// over all SMs shortens them more than the extra CTA rows lengthen the
+// cross-CTA sums (prostate: 145 CTAs of 384 threads, 25.4 us per iteration
+// against 28.7 us with 109 CTAs of 512); more voxels per thread (16, 32)
+// lengthen every per-voxel pass.
 vmat_status vmat_configure_master(vmat_ctx *ctx) {
   const int64_t Va = ctx->Va > 0 ? ctx->Va : 1;
   const int sms = ctx->sm_budget > 0 && ctx->sm_budget < ctx->num_sms ? ctx->sm_budget : ctx->num_sms;
-  const int target = sms < MASTER_CTA_TARGET ? sms : MASTER_CTA_TARGET;
+  const int target = sms;
   int vpt = 4;
   for (; vpt <= 32; vpt *= 2)
     if ((Va + (int64_t)vpt * 512 - 1) / ((int64_t)vpt * 512) <= sms) break;
