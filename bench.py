@@ -274,6 +274,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     l0 = plan.launches()
+    inf0 = vmat.vmat_get_info(plan.ctx)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record()
@@ -284,7 +285,20 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = plan.launches() - l0
+    inf1 = vmat.vmat_get_info(plan.ctx)
     ms, value = _aggregate(ev0.elapsed_time(ev1), ws, args.steps, cfg.iterations, "cuda")
+    # in-kernel phase clocks of the master (CTA 0) over the timed plans
+    pg_iters = inf1["master_pg_iters"] - inf0["master_pg_iters"]
+    master_phases = {
+        "us_per_iteration": {n: round(1e3 * (inf1["master_ms"][q] - inf0["master_ms"][q]) / max(pg_iters, 1), 3)
+                             for q, n in enumerate(["gradient_pass_and_sum", "step", "direction_pass",
+                                                    "line_search"])},
+        "grid_barriers_per_iteration": round((inf1["master_syncs"] - inf0["master_syncs"]) / max(pg_iters, 1), 3),
+        "note": "globaltimer clocks of CTA 0 inside k_master, per projected-gradient iteration",
+    }
+    live_calls = inf1["price_calls"][0] - inf0["price_calls"][0]
+    price_calls = inf1["price_calls"][1] - inf0["price_calls"][1]
+    live_entries = inf1["price_live_entries"] - inf0["price_live_entries"]
 
     # per-phase device time and the roofline of the dominant kernel
     phase = np.sum([r["phase_ms"] for r in recs], axis=0)  # [n_iter, 4]
@@ -294,6 +308,13 @@ def run_ours(args):
     mb = np.sum(mb, axis=0) / args.steps
     pb = np.sum(pb, axis=0) / args.steps
     db = np.sum(db, axis=0) / args.steps
+    if price_calls and live_calls == price_calls:
+        # every pricing read only the live voxels' rows: 8 B per entry read, F' read
+        # twice (scan, rows), and per free beamlet its accumulator read and cleared
+        # and its price written
+        free_beamlets = sum((cfg.n_angles - t) * cfg.n_rows * cfg.n_cols for t in range(cfg.iterations))
+        pb = np.array([(8.0 * live_entries + price_calls * 8.0 * info["n_active"]
+                        + args.steps * free_beamlets * 20.0) / args.steps])
     master_gbs = mb.sum() / (ph_tot[3] / 1e3) / 1e9
     price_gbs = pb.sum() / (ph_tot[0] / 1e3) / 1e9
     dom = int(np.argmax(ph_tot))
@@ -351,6 +372,15 @@ def run_ours(args):
     spmv["note"] = ("host-timed around the C-ABI call (includes its stream synchronisation); "
                     "bytes: 8 B/nnz (FP32 value + int32 index) + row pointers + vectors")
     spmv["price_in_plan_GB/s"] = round(price_gbs, 1)
+    spmv["price_in_plan"] = {
+        "ms_per_plan": round(float(ph_tot[0]), 3), "live_voxel_form_calls": int(live_calls),
+        "calls": int(price_calls),
+        "live_entries_per_call": round(live_entries / max(live_calls, 1), 1),
+        "fraction_of_D_read_per_call": round(live_entries / max(live_calls, 1) / prob.nnz, 5),
+        "note": ("prices of the free beams at each column-generation iteration; the live-voxel "
+                 "form reads only the voxel-major rows of voxels with F' != 0 (one-sided Eq. 1); "
+                 "GB/s over its algorithmic bytes (8 B per entry read + F' twice + 20 B per free "
+                 "beamlet)")}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
@@ -369,6 +399,7 @@ def run_ours(args):
            "master_method": {"pg": "projected gradient (Sec. 2.2)",
                              "newton": "projected Newton (option beyond the paper)"}[args.master],
            "master_iters_per_plan": int(np.mean([r["iters"].sum() for r in recs])),
+           "master_phases": master_phases,
            "final_cost": float(recs[-1]["cost"][-1]),
            "clocks": clocks}
 

@@ -101,6 +101,9 @@ typedef struct {
   int32_t n_subtiles;          /* subtiles per column (padded active voxels / subtile_voxels) */
   int64_t tile_entries[2];     /* union entries of the row tiles of D used by the batched
                                   products (voxel-major, beamlet-major; 0 until built) */
+  int64_t price_calls[2];      /* FP32 price products so far: [0] in the live-voxel form,
+                                  [1] in total (see vmat_set_price_path) */
+  int64_t price_live_entries;  /* entries of D read by the live-voxel calls so far */
 } vmat_info;
 
 /* Copy the problem to the device and build every storage form of D:
@@ -323,6 +326,30 @@ VMAT_API vmat_status vmat_set_master_precision(vmat_ctx *ctx, int32_t extended);
  * enqueued after the call (a batch re-captures its graph when it changes).
  * VMAT_EINVAL unless on is 0 or 1. */
 VMAT_API vmat_status vmat_set_price_smoothing(vmat_ctx *ctx, int32_t on);
+
+/* How the FP32 beamlet prices g = D f (Sec. 2.2) are formed, in vmat_price
+ * and in every pricing of vmat_colgen_run (the extended-precision master
+ * keeps its own FP64 row products).  Eq. 1 is one-sided, so at a master
+ * solution F'(z_j) = 0 for all but a few percent of the voxels.
+ *   VMAT_PRICE_AUTO (default): per call, on the device, the live-voxel form
+ *     when the voxel-major rows of the voxels with f_j != 0 hold at most 1/16
+ *     of D's entries, else the row products;
+ *   VMAT_PRICE_ROWS: always the beamlet-major row products (warp per row,
+ *     FP32 sums in the row's stored order);
+ *   VMAT_PRICE_LIVE: always the live-voxel form: only the voxel-major rows
+ *     with f_j != 0 are read; each product D_ij f_j (exact in FP64) is
+ *     rounded to a fixed-point step 2^-S and summed in a 64-bit integer per
+ *     beamlet, S chosen per call from max_j |f_j| and the largest row sum of
+ *     D so that no sum overflows.  Integer sums do not depend on the order
+ *     of the adds, so the result is deterministic; its error before the one
+ *     rounding to FP32 is below 1e-15 of max|f| x (largest row sum).  A
+ *     non-finite f falls back to the row products.
+ * Read by every call enqueued after it (a batch re-captures its graph when it
+ * changes).  VMAT_EINVAL for another value. */
+#define VMAT_PRICE_AUTO 0
+#define VMAT_PRICE_ROWS 1
+#define VMAT_PRICE_LIVE 2
+VMAT_API vmat_status vmat_set_price_path(vmat_ctx *ctx, int32_t path);
 
 /* Dose-rate feasibility of the final plan (Sec. 3).  Eq. 2 only penalises
  * the dose-rate variation between neighbouring beams; as a hard limit the

@@ -225,6 +225,7 @@ static std::vector<double> plan_settings(const vmat_batch *b) {
     v.push_back(c->master_method);
     v.push_back(c->master_xp);
     v.push_back(c->price_smoothing);
+    v.push_back(c->price_path);
   }
   return v;
 }

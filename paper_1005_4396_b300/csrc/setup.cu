@@ -413,6 +413,15 @@ extern "C" vmat_status vmat_set_price_smoothing(vmat_ctx *ctx, int32_t on) {
   return VMAT_OK;
 }
 
+extern "C" vmat_status vmat_set_price_path(vmat_ctx *ctx, int32_t path) {
+  if (!ctx) return VMAT_EINVAL;
+  if (path != VMAT_PRICE_AUTO && path != VMAT_PRICE_ROWS && path != VMAT_PRICE_LIVE)
+    return vmat_fail(ctx, VMAT_EINVAL, "price path must be 0 (auto), 1 (rows) or 2 (live voxels)");
+  VMAT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->price_path = path;
+  return VMAT_OK;
+}
+
 static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_t st,
                                vmat_ctx *ctx) {
   Tmp tmp;
@@ -530,6 +539,16 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->y, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->rho_plan, 1));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->g, B));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->pacc, B));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->pacc, 0, (size_t)B * 8, st));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->pstat, 6));
+  VMAT_CUDA(ctx, cudaMemsetAsync(ctx->pstat, 0, 48, st));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->plive, ctx->Va > 0 ? ctx->Va : 1));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->rowsum_max, 1));
+  {
+    vmat_status sr = vmat_row_sum_max(ctx);
+    if (sr != VMAT_OK) return sr;
+  }
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->xs, B));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->ap_price, N));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->ap_l, (size_t)N * R));
@@ -581,7 +600,7 @@ extern "C" void vmat_destroy(vmat_ctx *ctx) {
                   ctx->slot_beam, ctx->y, ctx->zact, ctx->fpact, ctx->rho_plan, ctx->g,
                   ctx->fgather, ctx->xs, ctx->ap_price, ctx->ap_l, ctx->ap_r, ctx->sel, ctx->sel_l,
                   ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats,
-                  ctx->hbuf};
+                  ctx->hbuf, ctx->pacc, ctx->pstat, ctx->rowsum_max, ctx->plive};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -607,6 +626,11 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
     cudaStreamSynchronize(ctx->stream);
     cudaMemcpy(ms, ctx->mstats, sizeof ms, cudaMemcpyDeviceToHost);
   }
+  unsigned long long pc[5] = {0, 0, 0, 0, 0};
+  if (ctx->pstat) cudaMemcpy(pc, ctx->pstat, sizeof pc, cudaMemcpyDeviceToHost);
+  out->price_calls[0] = (int64_t)pc[2];
+  out->price_calls[1] = (int64_t)pc[3];
+  out->price_live_entries = (int64_t)pc[4];
   for (int q = 0; q < 4; ++q) out->master_ms[q] = ms[q] * 1e-6;
   out->master_syncs = (int64_t)ms[4];
   out->master_pg_iters = (int64_t)ms[5];

@@ -8,6 +8,23 @@
 // D is streamed once per call (16-byte loads, evict-first); the dense vector
 // that is gathered (f or x, at most a few MB) stays resident in L2.
 // Dhat = D for FP32 storage; F16/BF16 store D_ij / s_i.
+//
+// Prices from the live voxels.  Eq. 1 is one-sided: F'(z_j) = 0 wherever a
+// voxel meets its threshold from the allowed side, which at a master
+// solution holds for all but ~1-2% of the voxels (the target and the few
+// organ or tissue voxels above their thresholds).  g = D F' then only needs
+// the voxel-major rows of the voxels with F'_j != 0: each entry D_ij F'_j
+// (an exact FP64 product of two floats) is rounded once to a fixed-point
+// grid of step 2^-S and added to beamlet i's 64-bit integer accumulator.
+// Integer addition is associative, so the sums do not depend on the order
+// in which the live rows' entries arrive (deterministic, although the adds
+// are atomic), and S is chosen per call from max|F'| and the largest row sum
+// of D so that no partial sum can overflow: every price carries an absolute
+// error below (entries of its row) x 2^-(S+1) ~ 1e-15 of that bound, below
+// the FP32 rounding of the result.  When the live rows hold more than 1/16
+// of D's entries the beamlet-major row products run instead.
+#include <algorithm>
+
 #include "vmat_internal.cuh"
 
 #define WARPS_PER_BLOCK 8
@@ -69,24 +86,6 @@ __device__ __forceinline__ float warp_row_dot(const int32_t *__restrict__ col,
 
 // ---------------------------------------------------------------- price
 // mode 0: all beams; 1: beams with mask[k] != 0; 2: beams with mask[k] == 0
-template <typename TV>
-__global__ void __launch_bounds__(256) k_price(const int64_t *__restrict__ ptr,
-                                               const int32_t *__restrict__ col,
-                                               const TV *__restrict__ val,
-                                               const float *__restrict__ scale, int use_scale,
-                                               const float *__restrict__ f,
-                                               const uint8_t *__restrict__ mask, int mode, int RC,
-                                               int64_t B, float *__restrict__ g) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-  if (i >= B) return;
-  if (mode) {
-    bool m = mask[i / RC] != 0;
-    if (m != (mode == 1)) return;
-  }
-  float acc = warp_row_dot<TV>(col, val, f, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
-  if (lane == 0) g[i] = use_scale ? acc * scale[i] : acc;
-}
 
 // Extended precision (the master's F' as the pair f + flo): g_i = s_i *
 // sum_j Dhat_ij (f_j + flo_j) accumulated in FP64, one warp per row, lanes
@@ -116,6 +115,196 @@ __global__ void __launch_bounds__(256) k_price_xp(const int64_t *__restrict__ pt
   if (lane == 0) g[i] = (float)(use_scale ? acc * (double)scale[i] : acc);
 }
 
+// ---------------------------------------------------------------- live-voxel prices
+// stat: [0] bits of max |f_j| (non-negative floats order like their bits),
+// [1] entries of the rows with f_j != 0, [5] number of those rows (these
+// three cleared before each call); [2] calls that took the live-voxel form,
+// [3] calls, [4] entries read by the live-voxel calls (cumulative).
+__device__ __forceinline__ bool price_sparse(const unsigned long long *stat, const double *rowsum_max,
+                                             int path, int64_t nnz, int &S) {
+  const double bound = (double)__uint_as_float((unsigned)stat[0]) * rowsum_max[0];
+  int e = 0;
+  frexp(bound, &e);  // bound < 2^e
+  S = bound > 0.0 ? 62 - e : 0;
+  if (!isfinite(bound)) return false;  // non-finite prices come from the row products
+  return path == VMAT_PRICE_LIVE || (path == VMAT_PRICE_AUTO && stat[1] * 16 <= (unsigned long long)nnz);
+}
+
+// beam of beamlet i: floor(i / RC) as (i * ceil(2^40 / RC)) >> 40, exact for
+// i < 2^23 and RC < 2^17 (the error i * delta / 2^40 < 2^-17 < 1 / RC)
+__device__ __forceinline__ int beam_of(unsigned i, unsigned long long rc_magic) {
+  return (int)(((unsigned long long)i * rc_magic) >> 40);
+}
+
+__device__ __forceinline__ bool mask_selected(const uint8_t *mask, int mode, int k) {
+  return mode == 0 || ((mask[k] != 0) == (mode == 1));
+}
+
+// round(d * f * 2^S) for finite floats d >= 0 and f, from the exact 48-bit
+// product of their significands (integer pipe; no FP64): ties away from zero.
+// The caller's S keeps |d f| 2^S below 2^62.
+__device__ __forceinline__ long long fixp_mul(float d, float f, int S) {
+  const unsigned bd = __float_as_uint(d), bf = __float_as_uint(f);
+  int ed = (int)((bd >> 23) & 0xffu), ef = (int)((bf >> 23) & 0xffu);
+  unsigned md = bd & 0x7fffffu, mf = bf & 0x7fffffu;
+  if (ed) md |= 0x800000u; else ed = 1;  // subnormals: no implicit bit, exponent of 1
+  if (ef) mf |= 0x800000u; else ef = 1;
+  const unsigned long long p = (unsigned long long)md * mf;  // d f = p 2^(ed + ef - 300)
+  const int sh = ed + ef - 300 + S;
+  unsigned long long v;
+  if (sh >= 0) v = p << sh;
+  else if (sh > -63) v = (p + (1ull << (-sh - 1))) >> (-sh);
+  else v = 0ull;
+  return (bf >> 31) ? -(long long)v : (long long)v;
+}
+
+// max |f|, the live rows' entry count and the list of live rows (in whatever
+// order the warps append them: the integer sums do not depend on it)
+__global__ void __launch_bounds__(256) k_price_scan(const float *__restrict__ f,
+                                                    const int64_t *__restrict__ vm_ptr, int32_t Va,
+                                                    unsigned long long *stat, int32_t *live) {
+  const int lane = threadIdx.x & 31;
+  unsigned fb = 0;
+  unsigned long long n = 0;
+  for (int32_t a0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; a0 < Va; a0 += gridDim.x * blockDim.x) {
+    const int32_t a = a0 + lane;
+    const float v = a < Va ? f[a] : 0.f;
+    const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
+    if (v != 0.f) {
+      fb = max(fb, __float_as_uint(fabsf(v)));
+      n += (unsigned long long)(vm_ptr[a + 1] - vm_ptr[a]);
+    }
+    if (m) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(stat + 5, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (v != 0.f) live[base + __popc(m & ((1u << lane) - 1u))] = a;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, o));
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+  }
+  if (lane == 0 && n) {
+    atomicMax(stat, (unsigned long long)fb);
+    atomicAdd(stat + 1, n);
+  }
+}
+
+// one warp per live row at a time (4 entries per lane in flight): each entry
+// of a selected beam goes to its beamlet's fixed-point accumulator
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price_live(const int64_t *__restrict__ vm_ptr,
+                                                    const int32_t *__restrict__ vm_col,
+                                                    const TV *__restrict__ vm_val,
+                                                    const float *__restrict__ f,
+                                                    const int32_t *__restrict__ live,
+                                                    const uint8_t *__restrict__ mask, int mode,
+                                                    unsigned long long rc_magic,
+                                                    const unsigned long long *__restrict__ stat,
+                                                    const double *__restrict__ rowsum_max, int path,
+                                                    int64_t nnz, unsigned long long *acc) {
+  int S;
+  if (!price_sparse(stat, rowsum_max, path, nnz, S)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5), nlive = (int64_t)stat[5];
+  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nlive; q += nw) {
+    const int32_t a = live[q];
+    const float fv = f[a];
+    const int64_t e1 = vm_ptr[a + 1];
+    for (int64_t e = vm_ptr[a] + lane; e < e1; e += 128) {
+      int32_t i[4];
+      float d[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = e + 32 * u < e1;
+        i[u] = in ? __ldcs(vm_col + e + 32 * u) : -1;
+        d[u] = in ? ld_stream(vm_val, e + 32 * u) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (i[u] < 0 || !mask_selected(mask, mode, beam_of((unsigned)i[u], rc_magic))) continue;
+        const long long v = fixp_mul(d[u], fv, S);
+        if (v) atomicAdd(acc + i[u], (unsigned long long)v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- price rows
+// Row products (warp per beamlet row, grid-stride) unless the call took the
+// live-voxel form; then each thread converts (and clears) the accumulators of
+// its beamlets.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_price_rows(const int64_t *__restrict__ ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const TV *__restrict__ val,
+                                                    const float *__restrict__ scale, int use_scale,
+                                                    const float *__restrict__ f,
+                                                    const uint8_t *__restrict__ mask, int mode, int RC,
+                                                    int64_t B, unsigned long long *stat,
+                                                    const double *__restrict__ rowsum_max, int path,
+                                                    int64_t nnz, unsigned long long *acc,
+                                                    float *__restrict__ g) {
+  int S;
+  const bool sparse = price_sparse(stat, rowsum_max, path, nnz, S);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    stat[3] += 1;
+    if (sparse) {
+      stat[2] += 1;
+      stat[4] += stat[1];
+    }
+  }
+  if (sparse) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      if (!mask_selected(mask, mode, (int)(i / RC))) continue;
+      const long long v = (long long)acc[i];
+      acc[i] = 0ull;
+      const double p = ldexp((double)v, -S);
+      g[i] = (float)(use_scale ? p * (double)scale[i] : p);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  for (int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); i < B; i += nw) {
+    if (!mask_selected(mask, mode, (int)(i / RC))) continue;
+    const float a = warp_row_dot<TV>(col, val, f, __ldg(ptr + i), __ldg(ptr + i + 1), lane);
+    if (lane == 0) g[i] = use_scale ? a * scale[i] : a;
+  }
+}
+
+// largest row sum of Dhat (FP64), for the fixed-point scale of the live-voxel prices
+template <typename TV>
+__global__ void k_row_sum_max(const int64_t *__restrict__ ptr, const TV *__restrict__ val, int64_t B,
+                              unsigned long long *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (i >= B) return;
+  double s = 0.0;
+  for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += 32) s += (double)vmat_ld(val, e);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+vmat_status vmat_row_sum_max(vmat_ctx *ctx) {
+  const unsigned nb = (unsigned)((ctx->B + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+  unsigned long long *out = (unsigned long long *)ctx->rowsum_max;
+  VMAT_CUDA(ctx, cudaMemsetAsync(out, 0, 8, ctx->stream));
+  if (nb == 0) return VMAT_OK;
+  if (ctx->dt == VMAT_F32)
+    k_row_sum_max<float><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, (const float *)ctx->bm_val, ctx->B, out);
+  else if (ctx->dt == VMAT_F16)
+    k_row_sum_max<__half><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, (const __half *)ctx->bm_val, ctx->B, out);
+  else
+    k_row_sum_max<__nv_bfloat16><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, (const __nv_bfloat16 *)ctx->bm_val,
+                                                               ctx->B, out);
+  VMAT_CUDA(ctx, cudaGetLastError());
+  ctx->n_launches += 1;
+  return VMAT_OK;
+}
+
 __global__ void k_gather_active(const float *__restrict__ full, const int32_t *__restrict__ act,
                                 int32_t Va, int32_t Vpad, float *__restrict__ out) {
   int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,17 +329,35 @@ vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *
                                                              (const __nv_bfloat16 *)ctx->bm_val,
                                                              ctx->scale, us, f_act, f_lo, mask, mode,
                                                              RC, B, g);
-  } else if (ctx->dt == VMAT_F32)
-    k_price<float><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col, (const float *)ctx->bm_val,
-                                                ctx->scale, us, f_act, mask, mode, RC, B, g);
-  else if (ctx->dt == VMAT_F16)
-    k_price<__half><<<nb, 256, 0, ctx->stream>>>(ctx->bm_ptr, ctx->bm_col,
-                                                 (const __half *)ctx->bm_val, ctx->scale, us, f_act,
-                                                 mask, mode, RC, B, g);
-  else
-    k_price<__nv_bfloat16><<<nb, 256, 0, ctx->stream>>>(
-        ctx->bm_ptr, ctx->bm_col, (const __nv_bfloat16 *)ctx->bm_val, ctx->scale, us, f_act, mask,
-        mode, RC, B, g);
+  } else {
+    // live-voxel form (or the row products when the live rows are not sparse)
+    cudaStream_t st = ctx->stream;
+    unsigned long long *stat = ctx->pstat;
+    VMAT_CUDA(ctx, cudaMemsetAsync(stat, 0, 16, st));
+    VMAT_CUDA(ctx, cudaMemsetAsync(stat + 5, 0, 8, st));
+    const unsigned nscan = (unsigned)std::min<int64_t>((ctx->Va + 255) / 256, 4 * ctx->num_sms);
+    k_price_scan<<<nscan > 0 ? nscan : 1, 256, 0, st>>>(f_act, ctx->vm_ptr, ctx->Va, stat, ctx->plive);
+    const int path = ctx->price_path;
+    const unsigned nlive = (unsigned)(8 * ctx->num_sms);  // persistent warps over the live rows
+    const unsigned nrows = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, 8 * ctx->num_sms));
+    const unsigned long long rc_magic = ((1ull << 40) + (unsigned long long)RC - 1) / (unsigned long long)RC;
+#define VMAT_PRICE_LAUNCH(TV)                                                                          \
+  k_price_live<TV><<<nlive, 256, 0, st>>>(ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, f_act,   \
+                                          ctx->plive, mask, mode, rc_magic, stat, ctx->rowsum_max,    \
+                                          path, ctx->nnz, ctx->pacc);                                 \
+  k_price_rows<TV><<<nrows, 256, 0, st>>>(ctx->bm_ptr, ctx->bm_col, (const TV *)ctx->bm_val, ctx->scale, \
+                                       us, f_act, mask, mode, RC, B, stat, ctx->rowsum_max, path,     \
+                                       ctx->nnz, ctx->pacc, g)
+    if (ctx->dt == VMAT_F32) {
+      VMAT_PRICE_LAUNCH(float);
+    } else if (ctx->dt == VMAT_F16) {
+      VMAT_PRICE_LAUNCH(__half);
+    } else {
+      VMAT_PRICE_LAUNCH(__nv_bfloat16);
+    }
+#undef VMAT_PRICE_LAUNCH
+    ctx->n_launches += 2;
+  }
   VMAT_CUDA(ctx, cudaGetLastError());
   ctx->n_launches += 1;
   return VMAT_OK;

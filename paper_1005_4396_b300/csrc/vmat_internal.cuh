@@ -116,6 +116,13 @@ struct vmat_ctx {
   size_t master_smem_pn = 0;   // shared memory of the projected-Newton variant
   float *hbuf = nullptr;       // projected Newton: [grid + 1][(N+1)(N+2)/2] Gram partials + sum
   int64_t hbuf_len = 0;
+  // live-voxel prices (spmv.cu)
+  int price_path = VMAT_PRICE_AUTO;
+  unsigned long long *pacc = nullptr;  // [B] fixed-point price accumulators, zero between calls
+  unsigned long long *pstat = nullptr; // [6] max|f| bits, live entries (per call); live-form
+                                       // calls, calls, live entries read (cumulative); live rows
+  int32_t *plive = nullptr;            // [Va] live rows of the current call
+  double *rowsum_max = nullptr;        // [1] largest row sum of Dhat
 };
 
 // ---------------------------------------------------------------- helpers
@@ -163,6 +170,7 @@ __device__ __forceinline__ float vmat_ld(const __nv_bfloat16 *p, int64_t e) {
 vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *mask, int mode,
                               float *g, const float *f_lo = nullptr);
 vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act);
+vmat_status vmat_row_sum_max(vmat_ctx *ctx);
 vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float *fp_full,
                              double *cost_dev);
 vmat_status vmat_launch_pricing(vmat_ctx *ctx, const float *g);

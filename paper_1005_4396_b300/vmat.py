@@ -50,7 +50,8 @@ class vmat_info(ctypes.Structure):
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
                 ("master_block", _i32), ("n_launches", _i64), ("master_ms", _d * 4),
                 ("master_syncs", _i64), ("master_pg_iters", _i64), ("subtile_voxels", _i32),
-                ("n_subtiles", _i32), ("tile_entries", _i64 * 2)]
+                ("n_subtiles", _i32), ("tile_entries", _i64 * 2), ("price_calls", _i64 * 2),
+                ("price_live_entries", _i64)]
 
 
 class vmat_column(ctypes.Structure):
@@ -101,6 +102,7 @@ EXPORTS = {
     "vmat_list_schedule": [_i32, _p, _p, _i32, _p, _p, _p, _p],
     "vmat_set_master_method": [_p, _i32],
     "vmat_set_price_smoothing": [_p, _i32],
+    "vmat_set_price_path": [_p, _i32],
     "vmat_set_master_precision": [_p, _i32],
     "vmat_dvh": [_p, _p, _d, _i32, _p],
     "vmat_dose_rate_feasibility": [_p, _d, _d, _i32, _i32, _d, _p, _p, _p, _p, _p],
@@ -195,6 +197,7 @@ def vmat_get_info(ctx) -> dict:
     out = {k: getattr(inf, k) for k, _ in vmat_info._fields_}
     out["master_ms"] = list(out["master_ms"])
     out["tile_entries"] = list(out["tile_entries"])
+    out["price_calls"] = list(out["price_calls"])
     return out
 
 
@@ -422,6 +425,12 @@ class Plan:
         instead of the beamlet sum alone (the default, as in the paper)."""
         vmat_set_price_smoothing(self.ctx, on)
 
+    def set_price_path(self, path="auto"):
+        """How the FP32 prices g = D f are formed: 'auto' (default), 'rows'
+        (beamlet-major row products) or 'live' (voxel-major rows of the
+        voxels with f != 0, fixed-point sums)."""
+        vmat_set_price_path(self.ctx, PRICE_PATHS[path])
+
     def set_profiling(self, on=True):
         vmat_set_profiling(self.ctx, on)
 
@@ -466,6 +475,13 @@ def vmat_set_master_precision(ctx, extended):
 
 def vmat_set_price_smoothing(ctx, on):
     _check(ctx, load_library().vmat_set_price_smoothing(ctx, int(bool(on))))
+
+
+PRICE_PATHS = {"auto": 0, "rows": 1, "live": 2}
+
+
+def vmat_set_price_path(ctx, path):
+    _check(ctx, load_library().vmat_set_price_path(ctx, int(path)))
 
 
 def vmat_dose_rate_feasibility(ctx, n_angles, max_rate, gamma_factor=2.0, max_rounds=20,

@@ -179,7 +179,12 @@ def test_prostate_whole_plan(prostate, pplan):
     cfg = prostate.cfg
     N, R, C, s = cfg.n_angles, cfg.n_rows, cfg.n_cols, cfg.max_leaf_step
     pplan.reset()
+    c0 = vmat.vmat_get_info(pplan.ctx)["price_calls"]
     out = pplan.colgen_run(kkt_tol=max(cfg.kkt_eps, 1e-6))
+    c1 = vmat.vmat_get_info(pplan.ctx)["price_calls"]
+    # F' is nonzero on a few percent of the voxels only: (nearly) every pricing
+    # read just their rows (live-voxel form, checked against the oracle below)
+    assert c1[1] - c0[1] == N and c1[0] - c0[0] >= 0.9 * N, (c0, c1)
     assert sorted(out["k"].tolist()) == list(range(N))
     y, ll, rr = out["y"], out["lleaf"], out["rleaf"]
     assert np.all(y >= 0)
@@ -209,6 +214,21 @@ def test_prostate_whole_plan(prostate, pplan):
     fp0 = oracle.voxel_dcost(np.zeros(prostate.n_vox), sid, T, al, be)
     rho_plan = (M @ np.abs(fp0)).max()  # bounds the first master's starting residual
     assert rho <= 1e-5 * reach + 2e-6 * rho_plan, (rho, reach, rho_plan)
+    # prices at the plan's F' (nonzero on the target and the voxels above their
+    # thresholds only): the automatic choice reads just those voxels' rows, and
+    # with D and F' FP32 on both sides each price is the exact one rounded once
+    # (up to the fixed-point grid, ~1e-15 of the bound)
+    fp32 = oracle.voxel_dcost(z.astype(np.float64), sid, T, al, be).astype(np.float32)
+    mask = (np.arange(N) % 2 == 0).astype(np.uint8)
+    c0 = vmat.vmat_get_info(pplan.ctx)["price_calls"]
+    gl = pplan.price(_cuda(fp32), mask).cpu().numpy()
+    c1 = vmat.vmat_get_info(pplan.ctx)["price_calls"]
+    assert c1[0] - c0[0] == 1 and c1[1] - c0[1] == 1, (c0, c1)
+    g_or = oracle.price(prostate, fp32.astype(np.float64), mask)
+    bound = np.abs(fp32).max() * oracle.price(prostate, np.ones(prostate.n_vox)).max()  # row sums
+    sel = mask[np.arange(prostate.n_beamlets) // (R * C)] != 0
+    assert np.all(np.abs(gl[sel] - g_or[sel]) <= 2.0 ** -24 * np.abs(g_or[sel]) + 1e-13 * bound)
+    assert np.all(gl[~sel] == 0)
     pplan.reset()
 
 
