@@ -294,6 +294,9 @@ def run_ours(args):
                              for q, n in enumerate(["gradient_pass_and_sum", "step", "direction_pass",
                                                     "line_search"])},
         "grid_barriers_per_iteration": round((inf1["master_syncs"] - inf0["master_syncs"]) / max(pg_iters, 1), 3),
+        "rejected_trial_steps_per_plan": round((inf1["master_rejected"] - inf0["master_rejected"]) / args.steps, 1),
+        "grid_barrier_wait_us_per_iteration": round(
+            1e3 * (inf1["master_wait_ms"] - inf0["master_wait_ms"]) / max(pg_iters, 1), 3),
         "note": "globaltimer clocks of CTA 0 inside k_master, per projected-gradient iteration",
     }
     live_calls = inf1["price_calls"][0] - inf0["price_calls"][0]
@@ -1010,6 +1013,8 @@ def run_case(args):
     cfg = inputs.prostate_config(nz=32)
     prob = inputs.make_problem(cfg)
     plan = vmat.Plan(prob, val_f32=True)
+    if args.case_ctas:
+        vmat.vmat_set_master_budget(plan.ctx, args.case_ctas)
     out = {"case": args.case, "nnz": prob.nnz, "active_voxels": plan.info["n_active"]}
     if args.case == "master":
         R = cfg.n_rows
@@ -1027,7 +1032,7 @@ def run_case(args):
         # stops early); its working set is that of the plan's hard masters
         rec = plan.colgen_run(n_iters=args.case_cols, kkt_tol=1e-6)
         res = plan.master_step(max_iters=30, kkt_tol=0.0)
-        info = plan.info
+        info = vmat.vmat_get_info(plan.ctx)
         sub = int(rec["col_subtiles"].sum())
         alg = (2 * 30 + 1) * sub * info["subtile_voxels"] * 4 + 8 * info["n_active"]
         out.update(columns=int(args.case_cols), master=res, nonzero_subtiles=sub,
@@ -1100,6 +1105,9 @@ def main():
                     help="small case for an ncu capture instead of the benchmark")
     ap.add_argument("--case-cols", type=int, default=150,
                     help="columns of the --case master launch (150: ~133 MB, above L2)")
+    ap.add_argument("--case-ctas", type=int, default=0,
+                    help="CTA budget of the --case master kernel (73 on the half-depth phantom "
+                         "gives the full prostate's 8 voxels per thread and 384-thread CTAs)")
     ap.add_argument("--batched", action="store_true",
                     help="the sixteen-plan batch (FP16-D, graph) against the FP32 single-plan loop")
     ap.add_argument("--batch-scale", type=float, default=1.0)

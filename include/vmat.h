@@ -96,7 +96,10 @@ typedef struct {
   double master_ms[4];         /* master kernel, cumulative device time (ms) in: gradient
                                   pass + its reduction, step, direction pass, line search */
   int64_t master_syncs;        /* cumulative grid-wide barriers of the master kernel */
-  int64_t master_pg_iters;     /* cumulative projected-gradient iterations */
+  double master_wait_ms;       /* cumulative time (ms) CTA 0 spent at those barriers between its
+                                  own arrival and the release (part of master_ms) */
+  int64_t master_pg_iters;     /* cumulative projected-gradient iterations (accepted steps) */
+  int64_t master_rejected;     /* cumulative trial steps the acceptance test cut back */
   int32_t subtile_voxels;      /* voxels per subtile of the aperture-dose columns */
   int32_t n_subtiles;          /* subtiles per column (padded active voxels / subtile_voxels) */
   int64_t tile_entries[2];     /* union entries of the row tiles of D used by the batched

@@ -45,6 +45,13 @@
 //            at 16 points (FP32 per voxel, compensated FP32 across warps and
 //            CTAs), one grid reduction per round; stop once Newton steps from both ends
 //            of the bracket agree (same linear piece: the secant is exact).
+//            Gradient projection takes the full step y + d first: the next
+//            pass A computes the gradient there and, in the same reduction,
+//            phi'(1); phi'(1) <= 0 makes t = 1 the minimiser (88% of a
+//            prostate plan's iterations), so the iteration needs one grid
+//            barrier.  Otherwise the rounds run from the saved point and the
+//            point moves to y + t d before another pass A.  The iterates are
+//            those of the line search at every step.
 // Stop: rho = max_k |min(y_k, g_k)| <= tol * max(rho_start, rho_ref).
 // The grid barrier is one counter whose top bit flips when every CTA has
 // arrived; each wait is bounded in time and spins, after which the kernel
@@ -54,6 +61,7 @@
 #include "vmat_internal.cuh"
 
 #define LS_POINTS 16
+#define MAX_WARPS 32
 #define LS_ROUNDS 4
 // per-CTA partial row: [N slots | 2 x 32 line-search values | cost | spare]
 #define PART_EXTRA 72
@@ -102,9 +110,10 @@ struct MasterArgs {
 // previous value (no reset).  Returns false if a wait ran out or another CTA
 // reported an error; the caller then leaves the kernel.
 __device__ __forceinline__ bool grid_sync(unsigned *bar, int *dstatus, unsigned long long wait_ns,
-                                          int *s_ok) {
+                                          int *s_ok, unsigned long long *wait_acc = nullptr) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned long long ta = wait_acc ? vmat_globaltimer() : 0ull;
     const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
     unsigned old, cur;
     int ok = 1;
@@ -127,6 +136,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *dstatus, unsigned 
     }
     if (ok && *(volatile int *)dstatus != 0) ok = 0;
     *s_ok = ok;
+    if (wait_acc) *wait_acc += vmat_globaltimer() - ta;  // arrival to release, as this CTA saw it
   }
   __syncthreads();
   return *s_ok != 0;
@@ -254,12 +264,16 @@ __device__ __forceinline__ int sid_of(const uint32_t (&sidw)[NW], int v) {
   return (int)((sidw[v >> 2] >> (8 * (v & 3))) & 0xffu);
 }
 
-template <int VPT>
-__device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[VPT],
-                                         const float (&w)[VPT], const uint32_t (&sid)[VPT / 4],
-                                         const float *s_tab, const float *s_t, float *s_rows,
-                                         float *s_ls, double *s_res, int *s_ok, int parity,
-                                         int stride, double &lsv) {
+// The first half of a round: the thread's voxels (their excess from e0(v),
+// their direction image w), the warp and CTA sums, and the CTA's 32 partials
+// written to its row of a.part (parity selects one of two row halves, so that
+// a round's partials are never overwritten while another CTA still reads the
+// previous round's).
+template <int VPT, typename E0>
+__device__ __forceinline__ void ls_eval(const MasterArgs &a, E0 e0_of, const float (&w)[VPT],
+                                        const uint32_t (&sid)[VPT / 4], const float *s_tab,
+                                        const float *s_t, float *s_rows, float *s_ls, int parity,
+                                        int stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   float t_first = s_t[0], t_last = s_t[0];
 #pragma unroll
@@ -278,7 +292,7 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     if (wq == 0.f) continue;
     const int id = sid_of(sid, q);
     const float al = s_tab[256 + id], be = s_tab[512 + id];
-    const float e0 = z[q];
+    const float e0 = e0_of(q);
     const float cw = wq > 0.f ? be : al;  // side taken at the threshold itself
     const float c0 = e0 > 0.f ? be : (e0 < 0.f ? al : cw);
     lin = fmaf(2.f * c0 * wq, wq, lin);
@@ -328,9 +342,17 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     for (int q = 0; q < nwarp; ++q) comp_add(cs, cc, s_ls[q * 32 + lane]);
     ((float *)(a.part + (size_t)blockIdx.x * stride + off))[lane] = __fadd_rn(cs, cc);
   }
-  if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_ok)) return false;
-  // sum the CTAs' partials: warp w takes CTAs w, w + W, ... (8 loads in flight
-  // per lane), compensated; then warp 0 combines the warps in order
+}
+
+// The second half, after the grid barrier: every CTA sums the CTAs' partials
+// (warp w takes CTAs w, w + W, ..., 8 loads in flight per lane,
+// compensated), then warp 0 combines the warps in order.  Out, in lane l of
+// warp 0 (lsv): sum_j D_j(t_l) for l < 16, sum_j 2 c_j(t_{l-16}) w_j^2 for
+// l >= 16.
+__device__ __forceinline__ void ls_gather(const MasterArgs &a, double *s_res, int parity, int stride,
+                                          double &lsv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int off = LS_OFF(a.N, parity);
   const int G = gridDim.x;
   float cs = 0.f, cc = 0.f;
   for (int c0 = warp; c0 < G; c0 += 8 * nwarp) {
@@ -355,7 +377,124 @@ __device__ __forceinline__ bool ls_round(const MasterArgs &a, const float (&z)[V
     }
     lsv = (double)S + (double)C;
   }
+}
+
+// One whole round: evaluation, grid barrier, gather.  Returns false if a wait
+// ran out or another CTA reported an error.
+template <int VPT, typename E0>
+__device__ __forceinline__ bool ls_round(const MasterArgs &a, E0 e0_of, const float (&w)[VPT],
+                                         const uint32_t (&sid)[VPT / 4], const float *s_tab,
+                                         const float *s_t, float *s_rows, float *s_ls, double *s_res,
+                                         int *s_ok, int parity, int stride, double &lsv,
+                                         unsigned long long *wait_acc) {
+  ls_eval<VPT>(a, e0_of, w, sid, s_tab, s_t, s_rows, s_ls, parity, stride);
+  if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_ok, wait_acc)) return false;
+  ls_gather(a, s_res, parity, stride, lsv);
   return true;
+}
+
+// Warp 0 after a round: lane p < 16 evaluates trial point p; the bracket
+// moves to the largest point with phi' < 0 and the smallest with phi' > 0
+// inside it (ties: lowest point index); every lane ends with the same state.
+// phi'(t) = phi'(0) + sum_j D_j(t) + 2 gamma G(d) t with phi'(0) = g.d and
+// G(d) from the warps' partials of the step phase (s_sc[32..], s_sc[48..]).
+// State: lo_t lo_f lo_h hi_t hi_f hi_h t done; done with t once the
+// minimiser is found (exact when both ends of the bracket lie on one linear
+// piece of phi', else the secant after LS_ROUNDS rounds).
+__device__ __forceinline__ void ls_bracket(int r, double lsv, const float *s_t, double *s_ls_state,
+                                           const double *s_sc, int nwarp, double gamma) {
+  const int lane = threadIdx.x & 31;
+  // lane p < 16 evaluates trial point p; the bracket moves to the
+  // largest point with phi' < 0 and the smallest with phi' > 0 inside
+  // it (ties: lowest point index); every lane ends with the same state
+  const unsigned FULL = 0xffffffffu;
+  // the warps' phi'(0) and G(d) partials, in order (same values every round)
+  float g0 = 0.f, gdd = 0.f;
+  for (int q = 0; q < nwarp; ++q) {
+    g0 += ((const float *)(s_sc + 32))[q];
+    gdd += ((const float *)(s_sc + 48))[q];
+  }
+  const double phi0 = (double)g0, cg1 = 2.0 * gamma * (double)gdd;
+  const int p = lane & (LS_POINTS - 1);
+  const bool in = lane < LS_POINTS;
+  const double tp = (double)s_t[p];
+  const double f = phi0 + __shfl_sync(FULL, lsv, p) + cg1 * tp;
+  const double h = __shfl_sync(FULL, lsv, p + LS_POINTS) + cg1;
+  double lo_t = s_ls_state[0], lo_f = r == 0 ? phi0 : s_ls_state[1], lo_h = s_ls_state[2];
+  double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
+  double t = -1.0;
+  if (r == 0 && !(phi0 < 0.0)) t = 0.0;  // not a descent direction
+  // an exact root among the points (round 0: before the full step t = 1)
+  const unsigned zero = __ballot_sync(FULL, in && f == 0.0 && (r > 0 || p < LS_POINTS - 1));
+  if (zero && t < 0.0) t = (double)s_t[__ffs(zero) - 1];
+  if (r == 0) {
+    lo_h = __shfl_sync(FULL, h, 0);  // slope just right of 0 (first point's side pattern)
+    const double f1 = __shfl_sync(FULL, f, LS_POINTS - 1), h1 = __shfl_sync(FULL, h, LS_POINTS - 1);
+    if (t < 0.0 && f1 <= 0.0) t = 1.0;
+    if (hi_h < 0.0) { hi_f = f1; hi_h = h1; }
+  }
+  if (t < 0.0) {
+    float key = (in && f < 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : -1.f;
+    int who = lane;
+    for (int o = 16; o; o >>= 1) {
+      const float k2 = __shfl_xor_sync(FULL, key, o);
+      const int w2 = __shfl_xor_sync(FULL, who, o);
+      if (k2 > key || (k2 == key && w2 < who)) { key = k2; who = w2; }
+    }
+    if (key >= 0.f) {
+      lo_t = __shfl_sync(FULL, tp, who);
+      lo_f = __shfl_sync(FULL, f, who);
+      lo_h = __shfl_sync(FULL, h, who);
+    }
+    key = (in && f > 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : 2.f;
+    who = lane;
+    for (int o = 16; o; o >>= 1) {
+      const float k2 = __shfl_xor_sync(FULL, key, o);
+      const int w2 = __shfl_xor_sync(FULL, who, o);
+      if (k2 < key || (k2 == key && w2 < who)) { key = k2; who = w2; }
+    }
+    if (key <= 1.f) {
+      hi_t = __shfl_sync(FULL, tp, who);
+      hi_f = __shfl_sync(FULL, f, who);
+      hi_h = __shfl_sync(FULL, h, who);
+    }
+    const double span = hi_t - lo_t;
+    const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
+    // Newton steps from both ends (FP32: they only test agreement)
+    const float na = lo_h > 0.0 ? (float)lo_t - (float)lo_f / (float)lo_h : -1.f;
+    const float nb = hi_h > 0.0 ? (float)hi_t - (float)hi_f / (float)hi_h : -2.f;
+    // both ends on one linear piece of phi' (their Newton steps agree): exact
+    if (!(span > 0.0) || fabsf(na - nb) <= 1e-6f * fabsf((float)tsec) || span <= 1e-7 * hi_t ||
+        r == LS_ROUNDS - 1)
+      t = tsec;
+  }
+  if (lane == 0) {
+    s_ls_state[0] = lo_t; s_ls_state[1] = lo_f; s_ls_state[2] = lo_h;
+    s_ls_state[3] = hi_t; s_ls_state[4] = hi_f; s_ls_state[5] = hi_h;
+    if (t >= 0.0) { s_ls_state[6] = fmin(fmax(t, lo_t), 1.0); s_ls_state[7] = 1.0; }
+  }
+}
+
+// Trial points of round r, by threads 0..15 (FP32, as they are stored):
+// round 0 at 1/16 .. 1; later rounds the Newton steps from both ends of the
+// bracket and 14 points across it (a step outside it falls back to a point
+// inside).  The caller synchronises before they are read.
+__device__ __forceinline__ void ls_points(int r, float *s_t, const double *s_ls_state) {
+  const int tid = threadIdx.x;
+  if (tid >= LS_POINTS) return;
+  float tq;
+  if (r == 0) {
+    tq = (float)(tid + 1) * (1.f / LS_POINTS);
+  } else {
+    const float lo_t = (float)s_ls_state[0], lo_f = (float)s_ls_state[1], lo_h = (float)s_ls_state[2];
+    const float hi_t = (float)s_ls_state[3], hi_f = (float)s_ls_state[4], hi_h = (float)s_ls_state[5];
+    const float span = hi_t - lo_t;
+    if (tid == 0) tq = lo_h > 0.f ? lo_t - lo_f / lo_h : -1.f;
+    else if (tid == 1) tq = hi_h > 0.f ? hi_t - hi_f / hi_h : -1.f;
+    else tq = lo_t + span * (float)(tid - 1) * (1.f / (LS_POINTS - 1));
+    if (!(tq > lo_t && tq < hi_t)) tq = lo_t + span * (tid == 0 ? 0.5f : 0.75f);
+  }
+  s_t[tid] = tq;
 }
 
 // Asynchronous 16-byte global -> shared copies (bypassing L1): a thread keeps
@@ -383,6 +522,12 @@ __device__ __forceinline__ void pair_dot(const float4 *Ms, const float4 *F4, int
 
 // Stages of the direction pass's copy pipeline: column segments in flight per thread
 __host__ __device__ constexpr int master_pipe_stages(int vpt) { return vpt >= 16 ? 8 : 16; }
+
+// Threads per CTA at most.  (768-thread CTAs at 4 voxels per thread, one
+// subtile per CTA, measured slower on the prostate plan: 37.8 against 25.3 us
+// per iteration; the CTAs holding the dense subtiles set the pace, and the
+// per-warp combinations of the step and the sums grow with the warp count.)
+__host__ __device__ constexpr int master_max_threads(int) { return 512; }
 
 // Floats of the region holding the line-search rows ([nthr][33]); the
 // direction pass runs its copy pipeline ([stages][nthr] float4) there, and
@@ -489,7 +634,7 @@ __device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z, flo
 }
 
 template <int VPT, bool NEWTON, bool XP>
-__global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
+__global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ns = a.nslots, tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -508,18 +653,20 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   double *s_igl = s_dy + N;          // [N] 1/gap to the left neighbour (0: none)
   double *s_igr = s_igl + N;         // [N] 1/gap to the right neighbour (0: none)
   int *s_slot = (int *)(s_igr + N);  // [N] slot of each beam, -1 if none (N doubles reserved)
-  double *s_sc = s_igr + 2 * N;      // [32] CTA-wide scalars
-  double *s_res = s_sc + 32;         // [32 + 16*32] line-search sums and scratch
+  // per-warp scratch below is sized for up to MAX_WARPS warps per CTA
+  double *s_sc = s_igr + 2 * N;      // [32 + 32] CTA-wide scalars, then per-warp phi'(0), G(d)
+  double *s_res = s_sc + 64;         // [32 + 32*32] line-search sums and scratch
   const int Np = (N + 1) & ~1;                    // keeps the float region below 16-byte aligned
-  float *s_yf = (float *)(s_res + 32 + 16 * 32);  // [Np] per slot
+  double *s_ysave = s_res + 32 + MAX_WARPS * 32;  // [Np] gradient projection: y at the accepted point
+  float *s_yf = (float *)(s_ysave + Np);          // [Np] per slot
   float *s_df = s_yf + Np;                        // [Np] per slot
   float *s_ylo = s_df + Np;                       // [Np4] low part of y
   float *s_tab = s_ylo + ((Np + 3) & ~3);         // [768]
   float *s_t = s_tab + 768;                       // [LS_POINTS] trial points
-  float *s_ls = s_t + LS_POINTS;                  // [16][32] warp partials
+  float *s_ls = s_t + LS_POINTS;                  // [MAX_WARPS][32] warp partials
   // s_fp is 16-byte aligned for its float4 accesses: the doubles above take a
-  // multiple of 16 bytes and the floats (2 Np + 1296) a multiple of 4
-  float *s_fp = s_ls + 16 * 32;  // [NG][ST] F' (pass A)
+  // multiple of 16 bytes and the floats (2 Np + 1808) a multiple of 4
+  float *s_fp = s_ls + MAX_WARPS * 32;  // [NG][ST] F' (pass A)
   float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
   const int rows_len = master_rows_len(N, nthr, VPT, NEWTON);
   float *s_pp = s_rows + rows_len;                // [N*NG] warp partial per (slot, subtile) pair
@@ -551,6 +698,12 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   float *s_fpl = s_xp;                            // [NG][ST] low part of F' (pass A)
   float *s_tablo = s_xp + NG * ST;                // [768] T, alpha, beta minus their FP32 values
   float *s_pplo = s_tablo + 768;                  // [N*NG] low part of each pair's dot product
+  // gradient projection only: the excess at the accepted point, [VPT][nthr]
+  // (and its low parts in extended precision), after the last region in use
+  float *s_zsave = (float *)(((uintptr_t)(NEWTON ? (void *)(s_cb + 2 * (N + 1))
+                                                 : (XP ? (void *)(s_pplo + N * NG) : (void *)(s_mcols + N * NG))) +
+                              15) & ~(uintptr_t)15);
+  float *s_zlsave = s_zsave + VPT * nthr;
 
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
   if (XP)
@@ -625,11 +778,18 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
   for (int q = 0; q < ABB_M - 1; ++q) bb2_hist[q] = INFINITY;
   bool alive = true;
   int ls_parity = 0;
+  // gradient projection: while `trial` holds, z and s_y are the full step
+  // (y + d, e + w) from the point saved in s_ysave / s_zsave, whose gradient
+  // the pass computes together with the first line-search round along d
+  bool trial = false;
+  int gpar = 0;        // which of the two sets of gradient rows this pass writes
+  int n_partial = 0;   // (CTA 0) steps whose exact minimiser was short of the full step
   // phase clocks of CTA 0, kept in shared memory (one thread uses them)
-  unsigned long long *s_clk = (unsigned long long *)(s_sc + 24);  // [5]: A, step, B, search, last
+  // [6]: A, step, B, search, last, grid-barrier waits (included in the phases)
+  unsigned long long *s_clk = (unsigned long long *)(s_sc + 24);
   const bool timer = blockIdx.x == 0 && tid == 0;
   if (timer)
-    for (int q = 0; q < 5; ++q) s_clk[q] = 0;
+    for (int q = 0; q < 6; ++q) s_clk[q] = 0;
 
   for (;;) {
     if (timer) s_clk[4] = vmat_globaltimer();
@@ -658,6 +818,34 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         f.w = dF_e(z[4 * m + 3], s_tab[256 + id], s_tab[512 + id]);
       }
       *(float4 *)(s_fp + m * ST + 4 * tid) = f;
+    }
+    if (!NEWTON && trial) {
+      // the line search's phi'(1) beyond phi'(0) + 2 gamma G(d): per voxel
+      // D_j(1) = 2 c_j(0) w_j^2 + 2 w_j (c' - c_j(0)) (e_j + w_j) if the voxel
+      // crosses its threshold before t = 1 (e_j + w_j is the excess now in z),
+      // reduced with the gradient (slot ns of the CTA rows)
+      float d1 = 0.f, d1c = 0.f;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const float wv = w[v];
+        if (wv == 0.f) continue;
+        const int id = sid_of(my_sid, v);
+        const float al = s_tab[256 + id], be = s_tab[512 + id];
+        const float e0 = s_zsave[v * nthr + tid], e1 = z[v];
+        const float cw = wv > 0.f ? be : al;  // side taken at the threshold itself
+        const float c0 = e0 > 0.f ? be : (e0 < 0.f ? al : cw);
+        float dv = 2.f * c0 * wv * wv;
+        const float dc = cw - c0;
+        if (dc != 0.f && e1 * wv > 0.f) dv = fmaf(2.f * wv * dc, e1, dv);
+        d1 += dv;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, d1, o), c2 = __shfl_xor_sync(0xffffffffu, d1c, o);
+        comp_add(d1, d1c, s2);
+        d1c = __fadd_rn(d1c, c2);
+      }
+      if (lane == 0) ((float2 *)(s_res + 32))[warp] = make_float2(d1, d1c);
     }
     __syncthreads();
     for (int q = warp; q < npairs; q += nwarp) {
@@ -711,17 +899,28 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       }
     }
     __syncthreads();
-    const int fstride = (N + 3) & ~3;
-    float *grow = a.gpart + (size_t)blockIdx.x * fstride;
+    const int fstride = (N + 4) & ~3;  // slots, then (gradient projection) phi'(1) at slot ns
+    // two sets of rows, alternating from one gradient pass to the next: the
+    // gradient projection passes only one grid barrier per iteration, so a
+    // CTA may write this pass's row while another still reads the last one
+    float *gp = a.gpart + (size_t)gpar * 2 * G * fstride;
+    float *grow = gp + (size_t)blockIdx.x * fstride;
     // extended precision: the low parts of the CTA rows follow all G rows
-    float *growlo = a.gpart + (size_t)(G + blockIdx.x) * fstride;
-    for (int s = tid; s < ((ns + 3) & ~3); s += nthr) {  // all-zero subtiles contribute exact zeros
+    float *growlo = gp + (size_t)(G + blockIdx.x) * fstride;
+    for (int s = tid; s < ((ns + 4) & ~3); s += nthr) {  // all-zero subtiles contribute exact zeros
       float cs = 0.f, cc = 0.f;
-      if (s < ns)
+      if (s < ns) {
         for (int q = s_pst[s]; q < s_pst[s + 1]; ++q) {
           comp_add(cs, cc, s_pp[q]);
           if (XP) cc = __fadd_rn(cc, s_pplo[q]);
         }
+      } else if (s == ns && !NEWTON && trial) {
+        for (int q = 0; q < nwarp; ++q) {
+          const float2 v = ((const float2 *)(s_res + 32))[q];
+          comp_add(cs, cc, v.x);
+          cc = __fadd_rn(cc, v.y);
+        }
+      }
       if (XP) {
         two_sum(cs, cc, grow[s], growlo[s]);
       } else {
@@ -729,11 +928,11 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
       }
     }
     ++nsync;
-    if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i)) { alive = false; break; }
+    if (!grid_sync(a.bar, a.dstatus, a.wait_ns, s_i, timer ? s_clk + 5 : nullptr)) { alive = false; break; }
     {  // every CTA sums every CTA's row in the same fixed order (compensated):
        // warp w takes CTAs w, w + W, ... (8 loads in flight per lane), lane l
        // slots 4l..4l+3 of each 128-slot chunk; then the warps are combined
-      const int n4 = (ns + 3) >> 2;
+      const int n4 = (ns + 4) >> 2;     // the slots and slot ns
       float2 *s_gw = (float2 *)s_rows;  // [nwarp][128] (the rows are free until pass B)
       for (int c4 = 0; c4 < n4; c4 += 32) {
         const int j = c4 + lane;
@@ -744,7 +943,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
           for (int u = 0; u < GB; ++u) {
             const int c = c0 + u * nwarp;
-            xv[u] = (c < G && j < n4) ? __ldcg((const float4 *)(a.gpart + (size_t)c * fstride) + j)
+            xv[u] = (c < G && j < n4) ? __ldcg((const float4 *)(gp + (size_t)c * fstride) + j)
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
@@ -759,7 +958,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
             for (int u = 0; u < GB; ++u) {
               const int c = c0 + u * nwarp;
               const float4 lo = (c < G && j < n4)
-                                    ? __ldcg((const float4 *)(a.gpart + (size_t)(G + c) * fstride) + j)
+                                    ? __ldcg((const float4 *)(gp + (size_t)(G + c) * fstride) + j)
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
               C[0] = __fadd_rn(C[0], lo.x);
               C[1] = __fadd_rn(C[1], lo.y);
@@ -771,19 +970,114 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) s_gw[warp * 128 + 4 * lane + e] = make_float2(S[e], C[e]);
         __syncthreads();
-        for (int t = tid; t < 128 && 4 * c4 + t < ns; t += nthr) {
+        for (int t = tid; t < 128 && 4 * c4 + t <= ns; t += nthr) {
           float gs = 0.f, gc = 0.f;
           for (int q = 0; q < nwarp; ++q) {
             const float2 v = s_gw[q * 128 + t];
             comp_add(gs, gc, v.x);
             gc = __fadd_rn(gc, v.y);
           }
-          s_g[4 * c4 + t] = (double)gs + (double)gc;  // M^T F'(z) of slot 4 c4 + t
+          if (4 * c4 + t < ns) s_g[4 * c4 + t] = (double)gs + (double)gc;  // M^T F'(z) of slot 4 c4 + t
+          else s_sc[16] = (double)gs + (double)gc;  // sum_j D_j(1) (gradient projection)
         }
         __syncthreads();
       }
     }
+    gpar ^= 1;
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[0] += c1 - s_clk[4]; s_clk[4] = c1; }
+
+    // ---------------- gradient projection: the exact line search along d.
+    // phi'(t) is nondecreasing, so t = 1 is its minimiser on [0, 1] exactly
+    // when phi'(1) = g.d + sum_j D_j(1) + 2 gamma G(d) <= 0 (most iterations);
+    // then the gradient just formed is the gradient at the new point and the
+    // step follows at once.  Otherwise the search runs its rounds from the
+    // saved point, the point moves to y + t d and a gradient pass follows.
+    if (!NEWTON && trial) {
+      double *s_ls_state = s_sc + 8;  // lo_t lo_f lo_h hi_t hi_f hi_h t done
+      if (tid == 0) {  // phi'(0) and G(d) from the warps' partials of the step phase, in order
+        float g0 = 0.f, gdd = 0.f;
+        for (int q = 0; q < nwarp; ++q) {
+          g0 += ((const float *)(s_sc + 32))[q];
+          gdd += ((const float *)(s_sc + 48))[q];
+        }
+        const double phi0 = (double)g0, f1 = phi0 + s_sc[16] + 2.0 * a.gamma * (double)gdd;
+        s_sc[17] = !(phi0 < 0.0) ? -1.0 : (f1 <= 0.0 ? 1.0 : 0.0);
+      }
+      __syncthreads();
+      const double verdict = s_sc[17];
+      const bool full = verdict > 0.0;
+      if (verdict == 0.0) {
+#pragma unroll
+        for (int p = 0; p < 33; ++p) s_rows[tid * 33 + p] = 0.f;  // the gradient sum used them
+        for (int r = 0; r < LS_ROUNDS && s_ls_state[7] == 0.0; ++r) {
+          ls_points(r, s_t, s_ls_state);
+          __syncthreads();
+          ++nsync;
+          double lsv = 0.0;
+          if (!ls_round<VPT>(a, [&](int q) { return s_zsave[q * nthr + tid]; }, w, my_sid, s_tab, s_t,
+                             s_rows, s_ls, s_res, s_i, ls_parity, stride, lsv, timer ? s_clk + 5 : nullptr)) {
+            alive = false;
+            break;
+          }
+          ls_parity ^= 1;
+          if (warp == 0) ls_bracket(r, lsv, s_t, s_ls_state, s_sc, nwarp, a.gamma);
+          __syncthreads();
+        }
+        if (!alive) break;
+      }
+      const double t = full ? 1.0 : (verdict < 0.0 ? 0.0 : (s_ls_state[6] >= 0.0 ? s_ls_state[6] : s_ls_state[0]));
+      const float tf = (float)t;
+      if (!full) {
+        // back to the saved point and along d by t (t <= 0: stay there)
+        const float tm = t > 0.0 ? tf : 0.f;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const float zs = s_zsave[v * nthr + tid];
+          if (XP) {  // (z, zl) = saved + tf w, the product's rounding error from an FMA
+            const float p = __fmul_rn(tm, w[v]), pe = __fmaf_rn(tm, w[v], -p);
+            float sh, se;
+            two_sum(zs, p, sh, se);
+            two_sum(sh, __fadd_rn(s_zlsave[v * nthr + tid], __fadd_rn(se, pe)), z[v], zl[XP ? v : 0]);
+          } else {
+            z[v] = fmaf(tm, w[v], zs);
+          }
+        }
+        for (int s = tid; s < ns; s += nthr) {
+          const int k = s_beam[s];
+          const double ys = s_ysave[k];
+          if (!(t > 0.0)) {
+            s_y[k] = ys;
+          } else if (XP) {  // a full step onto the bound lands on 0 exactly; never below it
+            const double yn = ys + (double)tf * (double)s_df[s];
+            s_y[k] = (yn <= 0.0 || (t == 1.0 && s_d[k] == -ys)) ? 0.0 : yn;
+          } else {
+            s_y[k] = ys + t * s_d[k];
+          }
+        }
+        if (timer) ++n_partial;
+      }
+      if (!(t > 0.0)) {
+        __syncthreads();
+        status = VMAT_ENOTCONV;
+        break;
+      }
+      // the move just made, for the next Barzilai-Borwein step; y as a float
+      // pair only before an iteration that refreshes e from it
+      ++it;
+      const bool pair_now = (it & 15) == 15;
+      for (int s = tid; s < ns; s += nthr) {
+        const int k = s_beam[s];
+        s_dy[s] = XP ? (double)tf * (double)s_df[s] : t * s_d[k];
+        if (pair_now) {
+          s_yf[s] = (float)s_y[k];
+          s_ylo[s] = (float)(s_y[k] - (double)s_yf[s]);
+        }
+      }
+      trial = false;
+      __syncthreads();
+      if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[3] += c1 - s_clk[4]; s_clk[4] = c1; }
+      if (!full) continue;  // the gradient at y + t d
+    }
 
     // ---------------- gradient, residual, direction (same in every CTA)
     // y, g and d are formed in FP64, spread over all threads.  The KKT
@@ -820,26 +1114,26 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         dgg += __shfl_xor_sync(FULL, dgg, o);
         dyy += __shfl_xor_sync(FULL, dyy, o);
       }
-      unsigned long long *s_ru = (unsigned long long *)(s_res + 32);  // [3][16]
-      float *s_rf = (float *)(s_res + 32 + 48);                       // [3][16]
+      unsigned long long *s_ru = (unsigned long long *)(s_res + 32);  // [3][MAX_WARPS]
+      float *s_rf = (float *)(s_res + 32 + 3 * MAX_WARPS);            // [3][MAX_WARPS]
       if (lane == 0) {
         s_ru[warp] = rb;
-        s_ru[16 + warp] = yb;
-        s_ru[32 + warp] = gb;
+        s_ru[MAX_WARPS + warp] = yb;
+        s_ru[2 * MAX_WARPS + warp] = gb;
         s_rf[warp] = dyg;
-        s_rf[16 + warp] = dgg;
-        s_rf[32 + warp] = dyy;
+        s_rf[MAX_WARPS + warp] = dgg;
+        s_rf[2 * MAX_WARPS + warp] = dyy;
       }
       __syncthreads();
       rb = yb = gb = 0;
       dyg = dgg = dyy = 0.f;
       for (int q = 0; q < nwarp; ++q) {
         rb = max(rb, s_ru[q]);
-        yb = max(yb, s_ru[16 + q]);
-        gb = max(gb, s_ru[32 + q]);
+        yb = max(yb, s_ru[MAX_WARPS + q]);
+        gb = max(gb, s_ru[2 * MAX_WARPS + q]);
         dyg += s_rf[q];
-        dgg += s_rf[16 + q];
-        dyy += s_rf[32 + q];
+        dgg += s_rf[MAX_WARPS + q];
+        dyy += s_rf[2 * MAX_WARPS + q];
       }
       rho = __longlong_as_double((long long)rb);
       if (it == 0) {
@@ -1102,7 +1396,7 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
             gd = fmaf((float)s_g[sl], (float)di, gd);
           }
           for (int o = 16; o; o >>= 1) gd += __shfl_xor_sync(FULL, gd, o);
-          float *s_gd = (float *)(s_res + 32 + 16);  // [nwarp]
+          float *s_gd = (float *)(s_res + 32 + MAX_WARPS);  // [nwarp]
           if (lane == 0) s_gd[warp] = gd;
           __syncthreads();
           gd = 0.f;
@@ -1145,8 +1439,8 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
         gdd += __shfl_xor_sync(FULL, gdd, o);
       }
       if (lane == 0) {  // summed over warps by warp 0 in the line search
-        ((float *)s_sc)[warp] = g0;               // s_sc[0..7]
-        ((float *)(s_sc + 16))[warp] = gdd;       // s_sc[16..23]
+        ((float *)(s_sc + 32))[warp] = g0;        // s_sc[32..47]
+        ((float *)(s_sc + 48))[warp] = gdd;       // s_sc[48..63]
       }
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[1] += c1 - s_clk[4]; s_clk[4] = c1; }
@@ -1246,111 +1540,56 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
     }
     if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[2] += c1 - s_clk[4]; s_clk[4] = c1; }
 
+    // ---------------- gradient projection: save the point and take the full
+    // step; the next gradient pass evaluates line-search round 0 along d
+    if (!NEWTON) {
+      for (int s = tid; s < ns; s += nthr) {
+        const int k = s_beam[s];
+        const double ys = s_y[k];
+        s_ysave[k] = ys;
+        if (XP) {  // a full step onto the bound lands on 0 exactly; never below it
+          const double yn = ys + (double)s_df[s];
+          s_y[k] = (yn <= 0.0 || s_d[k] == -ys) ? 0.0 : yn;
+        } else {
+          s_y[k] = ys + s_d[k];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        s_zsave[v * nthr + tid] = z[v];
+        if (XP) {
+          s_zlsave[v * nthr + tid] = zl[XP ? v : 0];
+          float sh, se;
+          two_sum(z[v], w[v], sh, se);
+          two_sum(sh, __fadd_rn(zl[XP ? v : 0], se), z[v], zl[XP ? v : 0]);
+        } else {
+          z[v] = fmaf(1.f, w[v], z[v]);
+        }
+      }
+      trial = true;
+      __syncthreads();
+      if (timer) { const unsigned long long c1 = vmat_globaltimer(); s_clk[3] += c1 - s_clk[4]; s_clk[4] = c1; }
+      continue;
+    }
+
     // ---------------- exact line search on [0, 1]
     // phi'(t) = phi'(0) + sum_j D_j(t) + 2 gamma G(d) t, phi'(0) = g.d from the
     // reduced gradient; warp 0 keeps the bracket [lo, hi] (phi'(lo) < 0 <
     // phi'(hi)) and threads 0..15 pick the trial points; all CTAs see the
     // same sums and take the same decisions.
     double *s_ls_state = s_sc + 8;  // lo_t lo_f lo_h hi_t hi_f hi_h t done
-    double phi0 = 0.0, cg1 = 0.0;   // phi'(0) and 2 gamma G(d): warp 0, from round 0 on
     for (int r = 0; r < LS_ROUNDS && s_ls_state[7] == 0.0; ++r) {
-      if (tid < LS_POINTS) {  // trial points (FP32, as they are stored)
-        float tq;
-        if (r == 0) {
-          tq = (float)(tid + 1) * (1.f / LS_POINTS);  // 1/16 .. 1
-        } else {
-          const float lo_t = (float)s_ls_state[0], lo_f = (float)s_ls_state[1], lo_h = (float)s_ls_state[2];
-          const float hi_t = (float)s_ls_state[3], hi_f = (float)s_ls_state[4], hi_h = (float)s_ls_state[5];
-          const float span = hi_t - lo_t;
-          if (tid == 0) tq = lo_h > 0.f ? lo_t - lo_f / lo_h : -1.f;
-          else if (tid == 1) tq = hi_h > 0.f ? hi_t - hi_f / hi_h : -1.f;
-          else tq = lo_t + span * (float)(tid - 1) * (1.f / (LS_POINTS - 1));
-          if (!(tq > lo_t && tq < hi_t)) tq = lo_t + span * (tid == 0 ? 0.5f : 0.75f);
-        }
-        s_t[tid] = tq;
-      }
+      ls_points(r, s_t, s_ls_state);
       __syncthreads();
       ++nsync;
       double lsv = 0.0;
-      if (!ls_round<VPT>(a, z, w, my_sid, s_tab, s_t, s_rows, s_ls, s_res, s_i, ls_parity, stride,
-                         lsv)) {
+      if (!ls_round<VPT>(a, [&](int q) { return z[q]; }, w, my_sid, s_tab, s_t, s_rows, s_ls, s_res,
+                         s_i, ls_parity, stride, lsv, timer ? s_clk + 5 : nullptr)) {
         alive = false;
         break;
       }
       ls_parity ^= 1;
-      if (warp == 0) {
-        // lane p < 16 evaluates trial point p; the bracket moves to the
-        // largest point with phi' < 0 and the smallest with phi' > 0 inside
-        // it (ties: lowest point index); every lane ends with the same state
-        const unsigned FULL = 0xffffffffu;
-        if (r == 0) {  // the warps' phi'(0) and G(d) partials, in order
-          float g0 = 0.f, gdd = 0.f;
-          for (int q = 0; q < nwarp; ++q) {
-            g0 += ((const float *)s_sc)[q];
-            gdd += ((const float *)(s_sc + 16))[q];
-          }
-          phi0 = (double)g0;
-          cg1 = 2.0 * a.gamma * (double)gdd;
-        }
-        const int p = lane & (LS_POINTS - 1);
-        const bool in = lane < LS_POINTS;
-        const double tp = (double)s_t[p];
-        const double f = phi0 + __shfl_sync(FULL, lsv, p) + cg1 * tp;
-        const double h = __shfl_sync(FULL, lsv, p + LS_POINTS) + cg1;
-        double lo_t = s_ls_state[0], lo_f = r == 0 ? phi0 : s_ls_state[1], lo_h = s_ls_state[2];
-        double hi_t = s_ls_state[3], hi_f = s_ls_state[4], hi_h = s_ls_state[5];
-        double t = -1.0;
-        if (r == 0 && !(phi0 < 0.0)) t = 0.0;  // not a descent direction
-        // an exact root among the points (round 0: before the full step t = 1)
-        const unsigned zero = __ballot_sync(FULL, in && f == 0.0 && (r > 0 || p < LS_POINTS - 1));
-        if (zero && t < 0.0) t = (double)s_t[__ffs(zero) - 1];
-        if (r == 0) {
-          lo_h = __shfl_sync(FULL, h, 0);  // slope just right of 0 (first point's side pattern)
-          const double f1 = __shfl_sync(FULL, f, LS_POINTS - 1), h1 = __shfl_sync(FULL, h, LS_POINTS - 1);
-          if (t < 0.0 && f1 <= 0.0) t = 1.0;
-          if (hi_h < 0.0) { hi_f = f1; hi_h = h1; }
-        }
-        if (t < 0.0) {
-          float key = (in && f < 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : -1.f;
-          int who = lane;
-          for (int o = 16; o; o >>= 1) {
-            const float k2 = __shfl_xor_sync(FULL, key, o);
-            const int w2 = __shfl_xor_sync(FULL, who, o);
-            if (k2 > key || (k2 == key && w2 < who)) { key = k2; who = w2; }
-          }
-          if (key >= 0.f) {
-            lo_t = __shfl_sync(FULL, tp, who);
-            lo_f = __shfl_sync(FULL, f, who);
-            lo_h = __shfl_sync(FULL, h, who);
-          }
-          key = (in && f > 0.0 && tp > lo_t && tp < hi_t) ? (float)tp : 2.f;
-          who = lane;
-          for (int o = 16; o; o >>= 1) {
-            const float k2 = __shfl_xor_sync(FULL, key, o);
-            const int w2 = __shfl_xor_sync(FULL, who, o);
-            if (k2 < key || (k2 == key && w2 < who)) { key = k2; who = w2; }
-          }
-          if (key <= 1.f) {
-            hi_t = __shfl_sync(FULL, tp, who);
-            hi_f = __shfl_sync(FULL, f, who);
-            hi_h = __shfl_sync(FULL, h, who);
-          }
-          const double span = hi_t - lo_t;
-          const double tsec = lo_t - lo_f * span / (hi_f - lo_f);
-          // Newton steps from both ends (FP32: they only test agreement)
-          const float na = lo_h > 0.0 ? (float)lo_t - (float)lo_f / (float)lo_h : -1.f;
-          const float nb = hi_h > 0.0 ? (float)hi_t - (float)hi_f / (float)hi_h : -2.f;
-          // both ends on one linear piece of phi' (their Newton steps agree): exact
-          if (!(span > 0.0) || fabsf(na - nb) <= 1e-6f * fabsf((float)tsec) || span <= 1e-7 * hi_t ||
-              r == LS_ROUNDS - 1)
-            t = tsec;
-        }
-        if (lane == 0) {
-          s_ls_state[0] = lo_t; s_ls_state[1] = lo_f; s_ls_state[2] = lo_h;
-          s_ls_state[3] = hi_t; s_ls_state[4] = hi_f; s_ls_state[5] = hi_h;
-          if (t >= 0.0) { s_ls_state[6] = fmin(fmax(t, lo_t), 1.0); s_ls_state[7] = 1.0; }
-        }
-      }
+      if (warp == 0) ls_bracket(r, lsv, s_t, s_ls_state, s_sc, nwarp, a.gamma);
       __syncthreads();
     }
     if (!alive) break;
@@ -1473,6 +1712,8 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
           a.stats[3] += (double)s_clk[3];
           a.stats[4] += (double)nsync;
           a.stats[5] += (double)it;
+          a.stats[6] += (double)s_clk[5];
+          a.stats[7] += (double)n_partial;
         }
       }
     }
@@ -1483,8 +1724,9 @@ __global__ void __launch_bounds__(512, 1) k_master(MasterArgs a) {
 // ---------------------------------------------------------------- launch
 static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton, bool xp) {
   const size_t ng = vpt / 4;
-  size_t b = (size_t)(8 * N + 32 + 32 + 16 * 32) * 8 +      // doubles: y d g gold dy igl igr slot sc res
-             (size_t)(2 * ((N + 1) & ~1) + ((((N + 1) & ~1) + 3) & ~3) + 768 + LS_POINTS + 16 * 32) * 4 +
+  size_t b = (size_t)(8 * N + 64 + 32 + MAX_WARPS * 32 + ((N + 1) & ~1)) * 8 +  // doubles: y d g gold dy
+                                                                                 // igl igr slot sc res ysave
+             (size_t)(2 * ((N + 1) & ~1) + ((((N + 1) & ~1) + 3) & ~3) + 768 + LS_POINTS + MAX_WARPS * 32) * 4 +
              (size_t)nthr * vpt * 4 +                          // F' tile
              (size_t)master_rows_len(N, nthr, vpt, newton) * 4 +  // line-search rows, pipeline, Newton
              (size_t)N * ng * 4 +                              // pair partials
@@ -1493,6 +1735,7 @@ static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton, bool xp) 
   if (newton) b += (size_t)(2 * N + 8 + ng * N) * 4 + (size_t)(2 * N + 2 * (N + 1)) * 4;
   if (xp) b += 16 + (size_t)nthr * vpt * 4 + 768 * 4 + (size_t)N * ng * 4;  // alignment, low parts:
                                                                             // F', T/alpha/beta, pairs
+  if (!newton) b += 16 + (size_t)nthr * vpt * 4 * (xp ? 2 : 1);  // excess at the accepted point
   return b + 16;
 }
 
@@ -1538,13 +1781,16 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   const int sms = ctx->sm_budget > 0 && ctx->sm_budget < ctx->num_sms ? ctx->sm_budget : ctx->num_sms;
   const int target = sms;
   int vpt = 4;
-  for (; vpt <= 32; vpt *= 2)
-    if ((Va + (int64_t)vpt * 512 - 1) / ((int64_t)vpt * 512) <= sms) break;
+  for (; vpt <= 32; vpt *= 2) {
+    const int64_t cap = (int64_t)vpt * master_max_threads(vpt);
+    if ((Va + cap - 1) / cap <= sms) break;
+  }
   if (vpt > 32) return vmat_fail(ctx, VMAT_EINVAL, "too many active voxels for the master kernel");
   const int64_t per = (Va + (int64_t)vpt * target - 1) / ((int64_t)vpt * target);
   int nthr = (int)(((per + 31) / 32) * 32);
   if (nthr < 256) nthr = 256;  // small problems: fewer CTAs of at least 8 warps
-  if (nthr > 512 || vpt >= 16) nthr = 512;  // at 16+ voxels per thread every warp counts
+  if (nthr > master_max_threads(vpt) || vpt >= 16)  // at 16+ voxels per thread every warp counts
+    nthr = master_max_threads(vpt);
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
   const bool xp = ctx->master_xp != 0;
@@ -1584,7 +1830,8 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
 // aligned) the per-CTA gradient partial rows [2 * grid][(N+3)&~3] floats
 int64_t vmat_master_scratch(int grid, int N) {
   // the gradient rows twice: value rows, then (extended precision) their low parts
-  return (int64_t)grid * (N + PART_EXTRA) + 2 + ((int64_t)2 * grid * ((N + 3) & ~3) + 1) / 2;
+  // (two sets of them: one per parity of the gradient pass)
+  return (int64_t)grid * (N + PART_EXTRA) + 2 + ((int64_t)4 * grid * ((N + 4) & ~3) + 1) / 2;
 }
 
 int64_t vmat_hessian_len(int N) { return (int64_t)(N + 1) * (N + 2) / 2; }

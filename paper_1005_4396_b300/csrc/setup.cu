@@ -633,7 +633,9 @@ extern "C" vmat_status vmat_get_info(const vmat_ctx *ctx, vmat_info *out) {
   out->price_live_entries = (int64_t)pc[4];
   for (int q = 0; q < 4; ++q) out->master_ms[q] = ms[q] * 1e-6;
   out->master_syncs = (int64_t)ms[4];
+  out->master_wait_ms = ms[6] * 1e-6;
   out->master_pg_iters = (int64_t)ms[5];
+  out->master_rejected = (int64_t)ms[7];
   out->tile_entries[0] = ctx->vtiles.n_union;
   out->tile_entries[1] = ctx->btiles.n_union;
   out->subtile_voxels = ctx->master_block * 4;

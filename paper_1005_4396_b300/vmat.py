@@ -49,7 +49,7 @@ class vmat_info(ctypes.Structure):
                 ("n_cols", _i32), ("n_beamlets", _i64), ("nnz", _i64), ("n_columns", _i32),
                 ("device_bytes", _i64), ("d_dtype", ctypes.c_int), ("master_grid", _i32),
                 ("master_block", _i32), ("n_launches", _i64), ("master_ms", _d * 4),
-                ("master_syncs", _i64), ("master_pg_iters", _i64), ("subtile_voxels", _i32),
+                ("master_syncs", _i64), ("master_wait_ms", _d), ("master_pg_iters", _i64), ("master_rejected", _i64), ("subtile_voxels", _i32),
                 ("n_subtiles", _i32), ("tile_entries", _i64 * 2), ("price_calls", _i64 * 2),
                 ("price_live_entries", _i64)]
 
