@@ -1125,45 +1125,61 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
         s_rf[2 * MAX_WARPS + warp] = dyy;
       }
       __syncthreads();
-      rb = yb = gb = 0;
-      dyg = dgg = dyy = 0.f;
-      for (int q = 0; q < nwarp; ++q) {
-        rb = max(rb, s_ru[q]);
-        yb = max(yb, s_ru[MAX_WARPS + q]);
-        gb = max(gb, s_ru[2 * MAX_WARPS + q]);
-        dyg += s_rf[q];
-        dgg += s_rf[MAX_WARPS + q];
-        dyy += s_rf[2 * MAX_WARPS + q];
-      }
-      rho = __longlong_as_double((long long)rb);
-      if (it == 0) {
-        rho0 = rho;
-        const double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
-        tol = a.kkt_tol * fmax(fmax(rho0, ref), 1e-300);
-      }
-      if (rho <= tol) { status = VMAT_OK; break; }
-      if (it >= a.max_iters) { status = VMAT_ENOTCONV; break; }
-      double step;
-      if (it == 0)
-        step = fmax(__longlong_as_double((long long)yb), 1.0) /
-               fmax(__longlong_as_double((long long)gb), 1e-300);
-      else {
-        // adaptive Barzilai-Borwein (ABBmin): where the two BB steps differ by
-        // more than the factor ABB_TAU the least of the last ABB_M short (BB2)
-        // steps, else the long (BB1) step; BB2 alone once a solve has taken
-        // ABB_ITERS iterations (the rare solves where the adaptive rule
-        // stalls then finish at BB2's pace)
-        const double bb2 = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
-        const double bb1 = dyg > 0.f ? (double)(dyy / dyg) : 1e12;
-        double hmin = bb2;
+      // one thread combines the warps and takes the scalar decisions (FP64
+      // issues at 1/64 of the FP32 rate on this GPU: redundant copies of this
+      // logic in every thread cost ~1 us per iteration); the others read them
+      if (tid == 0) {
+        rb = yb = gb = 0;
+        dyg = dgg = dyy = 0.f;
+        for (int q = 0; q < nwarp; ++q) {
+          rb = max(rb, s_ru[q]);
+          yb = max(yb, s_ru[MAX_WARPS + q]);
+          gb = max(gb, s_ru[2 * MAX_WARPS + q]);
+          dyg += s_rf[q];
+          dgg += s_rf[MAX_WARPS + q];
+          dyy += s_rf[2 * MAX_WARPS + q];
+        }
+        rho = __longlong_as_double((long long)rb);
+        if (it == 0) {
+          rho0 = rho;
+          const double ref = fmax(a.rho_ref, a.rho_plan ? *a.rho_plan : 0.0);
+          tol = a.kkt_tol * fmax(fmax(rho0, ref), 1e-300);
+        }
+        double step = 0.0, verdict = 0.0;
+        if (rho <= tol) {
+          verdict = 1.0;
+        } else if (it >= a.max_iters) {
+          verdict = 2.0;
+        } else if (it == 0) {
+          step = fmax(__longlong_as_double((long long)yb), 1.0) /
+                 fmax(__longlong_as_double((long long)gb), 1e-300);
+        } else {
+          // adaptive Barzilai-Borwein (ABBmin): where the two BB steps differ by
+          // more than the factor ABB_TAU the least of the last ABB_M short (BB2)
+          // steps, else the long (BB1) step; BB2 alone once a solve has taken
+          // ABB_ITERS iterations (the rare solves where the adaptive rule
+          // stalls then finish at BB2's pace)
+          const double bb2 = (dyg > 0.f && dgg >= 1e-30f) ? (double)(dyg / dgg) : 1e12;
+          const double bb1 = dyg > 0.f ? (double)(dyy / dyg) : 1e12;
+          double hmin = bb2;
 #pragma unroll
-        for (int q = 0; q < ABB_M - 1; ++q) hmin = fmin(hmin, bb2_hist[q]);
+          for (int q = 0; q < ABB_M - 1; ++q) hmin = fmin(hmin, bb2_hist[q]);
 #pragma unroll
-        for (int q = ABB_M - 2; q > 0; --q) bb2_hist[q] = bb2_hist[q - 1];
-        bb2_hist[0] = bb2;
-        step = it >= ABB_ITERS ? bb2 : (bb2 < ABB_TAU * bb1 ? hmin : bb1);
+          for (int q = ABB_M - 2; q > 0; --q) bb2_hist[q] = bb2_hist[q - 1];
+          bb2_hist[0] = bb2;
+          step = it >= ABB_ITERS ? bb2 : (bb2 < ABB_TAU * bb1 ? hmin : bb1);
+        }
+        s_sc[18] = fmin(fmax(step, 1e-12), 1e12);
+        s_sc[19] = verdict;
+        s_sc[20] = rho;
+        s_sc[21] = rho0;
       }
-      step = fmin(fmax(step, 1e-12), 1e12);
+      __syncthreads();
+      rho = s_sc[20];
+      rho0 = s_sc[21];
+      if (s_sc[19] == 1.0) { status = VMAT_OK; break; }
+      if (s_sc[19] == 2.0) { status = VMAT_ENOTCONV; break; }
+      const double step = s_sc[18];
       bool newton_ok = false;
       if (NEWTON) {
         // ---- projected Newton: the Hessian of Eq. 3 on the free set
