@@ -37,13 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
 # current kernel on the plan's own apertures (bench.py --case master-plan
-# --case-cols 90: 68.381952 MB read + 0.980992 MB written against 3,987,974,144
-# algorithmic bytes of that launch); set to None whenever the kernel changes
-# until it has been captured again
-MASTER_TRAFFIC_RATIO = (68.381952e6 + 0.980992e6) / 3987974144
-# L2 sector peak of that capture: 151.537635 sectors/ns at 13.936238% of peak
-# sustained elapsed, 32 B per sector
-L2_PEAK_GBS = 151.537635 / 0.13936238 * 32
+# --case-cols 90 --case-ctas 73: 69.286144 MB read + 1.085952 MB written
+# against 3,922,386,944 algorithmic bytes of that launch); set to None
+# whenever the kernel changes until it has been captured again
+MASTER_TRAFFIC_RATIO = (69.286144e6 + 1.085952e6) / 3922386944
+# L2 sector peak of that capture: 200,342,828 sectors in 1.547808 ms at
+# 11.895732% of peak sustained elapsed, 32 B per sector
+L2_PEAK_GBS = 200342828 / 1.547808e-3 / 0.11895732 * 32 / 1e9
 UNIT = "CG iters/s"
 
 
@@ -335,7 +335,7 @@ def run_ours(args):
                     if dom == 3 and MASTER_TRAFFIC_RATIO else None),
         "traffic_note": "per launch (average over the plan), scaled from one ncu capture of the "
                         "same kernel on a half-depth prostate plan's own 90 apertures (65 MB of "
-                        "nonzero column subtiles, L2-resident): DRAM/algorithmic = 0.0174",
+                        "nonzero column subtiles, L2-resident): DRAM/algorithmic = 0.0179",
         "l2": ({"achieved": round(dom_gbs, 1), "peak": round(L2_PEAK_GBS, 1), "unit": "GB/s",
                 "frac": round(dom_gbs / L2_PEAK_GBS, 4),
                 "peak_kind": "L2 sector peak of the ncu capture (34.8 TB/s)"} if dom == 3 else None),
@@ -1038,6 +1038,25 @@ def run_case(args):
         out.update(columns=int(args.case_cols), master=res, nonzero_subtiles=sub,
                    nonzero_column_MB=round(sub * info["subtile_voxels"] * 4 / 1e6, 2),
                    algorithmic_bytes_last_launch=alg, master_launch=[info["master_grid"], info["master_block"]])
+    elif args.case == "price-live":
+        # prices at a plan's F' (live-voxel form): --case-cols column-generation
+        # iterations (one live-voxel pricing each), then three stand-alone price
+        # calls at F' of the plan dose, F' formed here in NumPy (Eq. 1, FP32)
+        plan.colgen_run(n_iters=args.case_cols, kkt_tol=1e-6)
+        z = plan.plan_dose().cpu().numpy().astype(np.float64)
+        e = z - prob.T[prob.struct_id]
+        fp = np.where(e > 0, 2 * prob.beta[prob.struct_id] * e,
+                      np.where(e < 0, 2 * prob.alpha[prob.struct_id] * e, 0.0)).astype(np.float32)
+        f = torch.as_tensor(fp, device="cuda")
+        i0 = vmat.vmat_get_info(plan.ctx)
+        for _ in range(3):
+            plan.price(f)
+        torch.cuda.synchronize()
+        i1 = vmat.vmat_get_info(plan.ctx)
+        calls = i1["price_calls"][0] - i0["price_calls"][0]
+        out.update(columns=int(args.case_cols), live_voxels=int(np.count_nonzero(fp)),
+                   live_form_calls=int(calls),
+                   live_entries_per_call=int((i1["price_live_entries"] - i0["price_live_entries"]) / max(calls, 1)))
     elif args.case == "spmm32":
         # the differentiable forward's batched products: 32 fluence vectors
         X = torch.rand(prob.n_beamlets, 32, device="cuda")
@@ -1101,7 +1120,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the head-and-neck and batched workloads of the default run")
-    ap.add_argument("--case", default=None, choices=["master", "master-plan", "spmv", "spmm32"],
+    ap.add_argument("--case", default=None, choices=["master", "master-plan", "spmv", "spmm32", "price-live"],
                     help="small case for an ncu capture instead of the benchmark")
     ap.add_argument("--case-cols", type=int, default=150,
                     help="columns of the --case master launch (150: ~133 MB, above L2)")
