@@ -339,7 +339,7 @@ vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *
     k_price_scan<<<nscan > 0 ? nscan : 1, 256, 0, st>>>(f_act, ctx->vm_ptr, ctx->Va, stat, ctx->plive);
     const int path = ctx->price_path;
     const unsigned nlive = (unsigned)(8 * ctx->num_sms);  // persistent warps over the live rows
-    const unsigned nrows = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, 8 * ctx->num_sms));
+    const unsigned nrows = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, 32 * ctx->num_sms));
     const unsigned long long rc_magic = ((1ull << 40) + (unsigned long long)RC - 1) / (unsigned long long)RC;
 #define VMAT_PRICE_LAUNCH(TV)                                                                          \
   k_price_live<TV><<<nlive, 256, 0, st>>>(ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, f_act,   \
