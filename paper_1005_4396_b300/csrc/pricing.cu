@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
                                                   const int16_t *__restrict__ sr,
                                                   float *__restrict__ Mcol,
                                                   float *__restrict__ Mcol_lo, int tile,
-                                                  int32_t *__restrict__ tflag) {
+                                                  int32_t *__restrict__ tflag,
+                                                  const uint16_t *__restrict__ boff, int N1) {
   __shared__ int16_t L[VMAT_MAX_ROWS], Rr[VMAT_MAX_ROWS];
   __shared__ int sk;
   if (threadIdx.x == 0) sk = sel->status == 0 ? sel->k : -1;
@@ -267,13 +268,20 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
     return;  // padding and failed selections leave the tile flags alone
   }
   const int32_t RC = R * C, lo = k * RC, hi = lo + RC;
-  int64_t b = ptr[a], e = ptr[a + 1];
-  while (b < e) {  // first entry with beamlet >= lo
-    int64_t m = (b + e) >> 1;
-    if (col[m] < lo) b = m + 1;
-    else e = m;
+  int64_t b = ptr[a], end;
+  if (boff) {  // the row's entries of beam k, from the offsets table
+    const uint16_t *o = boff + (size_t)a * N1 + k;
+    end = b + o[1];
+    b += o[0];
+  } else {
+    int64_t e = ptr[a + 1];
+    end = e;
+    while (b < e) {  // first entry with beamlet >= lo
+      int64_t m = (b + e) >> 1;
+      if (col[m] < lo) b = m + 1;
+      else e = m;
+    }
   }
-  const int64_t end = ptr[a + 1];
   float accf = 0.f;   // FP32 sum in beamlet order
   double acc = 0.0;   // extended precision: FP64 sum, kept as a float pair
   for (int64_t q = b; q < end; ++q) {
@@ -295,6 +303,60 @@ __global__ void __launch_bounds__(256) k_aperture(const int64_t *__restrict__ pt
   // (subtiles are whole multiples of 128 voxels: a warp never straddles two)
   if (__any_sync(__activemask(), accf != 0.f) && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
     atomicOr(tflag + a / tile, 1);
+}
+
+// Offsets of each beam's entries in each voxel-major row: boff[a][k] = the
+// number of entries of row a with beamlet < k * RC (k = 0..N; rows are sorted
+// by beamlet).  One warp per row; entry e writes the offsets of the beams
+// from the previous entry's beam (exclusive) to its own.  Rows longer than
+// 65,535 entries do not fit and set *overflow.
+__global__ void __launch_bounds__(256) k_beam_offsets(const int64_t *__restrict__ ptr,
+                                                      const int32_t *__restrict__ col, int32_t Va,
+                                                      int N, unsigned long long rc_magic,
+                                                      uint16_t *__restrict__ boff, int *overflow) {
+  const int lane = threadIdx.x & 31;
+  const int32_t a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (a >= Va) return;
+  const int64_t s = ptr[a], t = ptr[a + 1];
+  if (t - s > 65535) {
+    if (lane == 0) atomicExch(overflow, 1);
+    return;
+  }
+  uint16_t *o = boff + (size_t)a * (N + 1);
+  for (int64_t e = s + lane; e < t; e += 32) {
+    const int bcur = (int)(((unsigned long long)(unsigned)col[e] * rc_magic) >> 40);
+    const int bprev = e == s ? -1 : (int)(((unsigned long long)(unsigned)col[e - 1] * rc_magic) >> 40);
+    for (int k = bprev + 1; k <= bcur; ++k) o[k] = (uint16_t)(e - s);
+  }
+  if (lane == 0) {
+    const int blast = t > s ? (int)(((unsigned long long)(unsigned)col[t - 1] * rc_magic) >> 40) : -1;
+    for (int k = blast + 1; k <= N; ++k) o[k] = (uint16_t)(t - s);
+  }
+}
+
+vmat_status vmat_build_beam_offsets(vmat_ctx *ctx) {
+  cudaStream_t st = ctx->stream;
+  const int RC = ctx->R * ctx->C;
+  const unsigned long long magic = ((1ull << 40) + (unsigned long long)RC - 1) / (unsigned long long)RC;
+  int *flag = (int *)(ctx->pstat + 5);  // the live-row count word, free outside a price call
+  VMAT_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), st));
+  VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->vm_boff, (size_t)(ctx->Va > 0 ? ctx->Va : 1) * (ctx->N + 1)));
+  if (ctx->Va > 0) {
+    k_beam_offsets<<<(unsigned)((ctx->Va + 7) / 8), 256, 0, st>>>(ctx->vm_ptr, ctx->vm_col, ctx->Va, ctx->N,
+                                                                  magic, ctx->vm_boff, flag);
+    ctx->n_launches += 1;
+  }
+  int h = 0;
+  VMAT_CUDA(ctx, cudaGetLastError());
+  VMAT_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VMAT_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), st));
+  VMAT_CUDA(ctx, cudaStreamSynchronize(st));
+  if (h) {  // a row too long for 16-bit offsets: the aperture kernel bisects instead
+    cudaFree(ctx->vm_boff);
+    ctx->device_bytes -= (int64_t)((size_t)ctx->Va * (ctx->N + 1) * sizeof(uint16_t));
+    ctx->vm_boff = nullptr;
+  }
+  return VMAT_OK;
 }
 
 // commit the selected aperture as plan column `slot`
@@ -340,7 +402,7 @@ vmat_status vmat_launch_add_column(vmat_ctx *ctx, int slot, int32_t *rec_subtile
   int us = ctx->dt != VMAT_F32;
 #define VMAT_AP_ARGS                                                                              \
   ctx->vm_ptr, ctx->vm_col, (const TV *)ctx->vm_val, ctx->scale, us, ctx->Va, ctx->Vpad, ctx->R, \
-      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol, Mcol_lo, tile, tf
+      ctx->C, ctx->sel, ctx->sel_l, ctx->sel_r, Mcol, Mcol_lo, tile, tf, ctx->vm_boff, ctx->N + 1
   if (ctx->dt == VMAT_F32) {
     typedef float TV;
     k_aperture<TV><<<nb, 256, 0, st>>>(VMAT_AP_ARGS);

@@ -548,6 +548,8 @@ static vmat_status create_impl(const vmat_problem *P, vmat_dtype dt, cudaStream_
   {
     vmat_status sr = vmat_row_sum_max(ctx);
     if (sr != VMAT_OK) return sr;
+    sr = vmat_build_beam_offsets(ctx);
+    if (sr != VMAT_OK) return sr;
   }
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->xs, B));
   VMAT_CUDA(ctx, vmat_alloc(ctx, &ctx->ap_price, N));
@@ -600,7 +602,7 @@ extern "C" void vmat_destroy(vmat_ctx *ctx) {
                   ctx->slot_beam, ctx->y, ctx->zact, ctx->fpact, ctx->rho_plan, ctx->g,
                   ctx->fgather, ctx->xs, ctx->ap_price, ctx->ap_l, ctx->ap_r, ctx->sel, ctx->sel_l,
                   ctx->sel_r, ctx->red, ctx->mout, ctx->bar, ctx->dstatus, ctx->mstats,
-                  ctx->hbuf, ctx->pacc, ctx->pstat, ctx->rowsum_max, ctx->plive};
+                  ctx->hbuf, ctx->pacc, ctx->pstat, ctx->rowsum_max, ctx->plive, ctx->vm_boff};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;

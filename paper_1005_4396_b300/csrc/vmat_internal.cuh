@@ -70,6 +70,7 @@ struct vmat_ctx {
   int32_t *bm_col = nullptr;
   void *bm_val = nullptr;
   int64_t *vm_ptr = nullptr;   // [Va+1] voxel-major CSR, rows sorted by beamlet
+  uint16_t *vm_boff = nullptr; // [Va][N+1] offset of each beam's entries in its row (or NULL)
   int32_t *vm_col = nullptr;
   void *vm_val = nullptr;
 
@@ -171,6 +172,7 @@ vmat_status vmat_launch_price(vmat_ctx *ctx, const float *f_act, const uint8_t *
                               float *g, const float *f_lo = nullptr);
 vmat_status vmat_gather_active(vmat_ctx *ctx, const float *full, float *act);
 vmat_status vmat_row_sum_max(vmat_ctx *ctx);
+vmat_status vmat_build_beam_offsets(vmat_ctx *ctx);
 vmat_status vmat_launch_dose(vmat_ctx *ctx, const float *x, float *z_full, float *fp_full,
                              double *cost_dev);
 vmat_status vmat_launch_pricing(vmat_ctx *ctx, const float *g);
