@@ -588,48 +588,63 @@ __device__ bool chol_packed_aug(float *A, int n, float *cb, float *dg) {
 // column entry with y (a float pair) enters through dot2_add.  Near the
 // solution many voxels sit close to their thresholds; there e is small and
 // this keeps it exact to a few units of its own last place, where plain FP32
-// sums of z would carry errors of the size of T's.
-template <int VPT>
+// sums of z would carry errors of the size of T's.  Each subtile's nonzero
+// columns (ascending slots, the order of the direction pass's refresh) stream
+// through the shared-memory ring `pipe` of STG copies per thread; the caller
+// waits for the ring to drain before reusing it.
+template <int VPT, bool XP, int STG>
 __device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z, float *zlo,
                                               const uint32_t (&my_sid)[VPT / 4], const float *s_tab,
-                                              const float *s_tablo, const int *s_nz, const int *s_mask,
-                                              const float *s_yf, const float *s_ylo, int nnzs,
-                                              size_t off0, size_t mstride) {
+                                              const float *s_tablo, const int *s_mcnt,
+                                              const int *s_mcols, int N, const float *s_yf,
+                                              const float *s_ylo, float4 *pipe, size_t off0,
+                                              size_t mstride) {
   constexpr int NG = VPT / 4;
-  float zc[VPT];
+  const int tid = threadIdx.x, nthr = blockDim.x;
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    z[v] = -s_tab[sid_of(my_sid, v)];
-    zc[v] = s_tablo ? -s_tablo[sid_of(my_sid, v)] : 0.f;  // extended: T as a float pair
-  }
-  for (int q = 0; q < nnzs; ++q) {
-    const int s = s_nz[q], mk = s_mask[s];
-    const float *Ms = a.M + (size_t)s * a.Vpad + off0;
-    const float ys = s_yf[s], yl = s_ylo[s];
+  for (int m = 0; m < NG; ++m) {
+    const int nm = s_mcnt[m];
+    const int *cl = s_mcols + m * N;
+    const float *src = a.M + off0 + m * mstride + 4 * tid;
+    float zz[4], zc[4];
 #pragma unroll
-    for (int m = 0; m < NG; ++m) {
-      if (!(mk >> m & 1)) continue;
-      const float4 c = __ldg((const float4 *)(Ms + m * mstride) + threadIdx.x);
-      dot2_add(z[4 * m], zc[4 * m], c.x, ys, yl);
-      dot2_add(z[4 * m + 1], zc[4 * m + 1], c.y, ys, yl);
-      dot2_add(z[4 * m + 2], zc[4 * m + 2], c.z, ys, yl);
-      dot2_add(z[4 * m + 3], zc[4 * m + 3], c.w, ys, yl);
-      if (zlo) {  // extended precision: the columns' low parts
-        const float4 cl = __ldg((const float4 *)(a.Mlo + (size_t)s * a.Vpad + off0 + m * mstride) +
-                                threadIdx.x);
-        zc[4 * m] = fmaf(cl.x, ys, zc[4 * m]);
-        zc[4 * m + 1] = fmaf(cl.y, ys, zc[4 * m + 1]);
-        zc[4 * m + 2] = fmaf(cl.z, ys, zc[4 * m + 2]);
-        zc[4 * m + 3] = fmaf(cl.w, ys, zc[4 * m + 3]);
-      }
+    for (int q = 0; q < 4; ++q) {
+      zz[q] = -s_tab[sid_of(my_sid, 4 * m + q)];
+      zc[q] = XP ? -s_tablo[sid_of(my_sid, 4 * m + q)] : 0.f;  // extended: T as a float pair
     }
-  }
-  if (zlo) {  // extended precision: keep the excess as the pair (z, zlo)
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) two_sum(z[v], zc[v], z[v], zlo[v]);
-  } else {
+    for (int k = 0; k < STG; ++k) {
+      if (k < nm) cp_async16(pipe + k * nthr + tid, src + (size_t)cl[k] * a.Vpad);
+      cp_async_commit();
+    }
+    for (int q = 0; q < nm; ++q) {
+      cp_async_wait<STG - 1>();
+      const int slot = q & (STG - 1);
+      const float4 v = pipe[slot * nthr + tid];
+      const int sl = cl[q];
+      const float ys = s_yf[sl], yl = s_ylo[sl];
+      dot2_add(zz[0], zc[0], v.x, ys, yl);
+      dot2_add(zz[1], zc[1], v.y, ys, yl);
+      dot2_add(zz[2], zc[2], v.z, ys, yl);
+      dot2_add(zz[3], zc[3], v.w, ys, yl);
+      if (XP) {  // extended precision: the columns' low parts
+        const float4 vl =
+            __ldg((const float4 *)(a.Mlo + off0 + m * mstride + (size_t)sl * a.Vpad) + tid);
+        zc[0] = fmaf(vl.x, ys, zc[0]);
+        zc[1] = fmaf(vl.y, ys, zc[1]);
+        zc[2] = fmaf(vl.z, ys, zc[2]);
+        zc[3] = fmaf(vl.w, ys, zc[3]);
+      }
+      if (q + STG < nm) cp_async16(pipe + slot * nthr + tid, src + (size_t)cl[q + STG] * a.Vpad);
+      cp_async_commit();
+    }
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) z[v] = __fadd_rn(z[v], zc[v]);
+    for (int q = 0; q < 4; ++q) {
+      if (XP)  // keep the excess as the pair (z, zlo)
+        two_sum(zz[q], zc[q], z[4 * m + q], zlo[4 * m + q]);
+      else
+        z[4 * m + q] = __fadd_rn(zz[q], zc[q]);
+    }
   }
 }
 
@@ -670,10 +685,9 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
   float *s_rows = s_fp + NG * ST;                 // [nthr][33] line-search rows, kept zero between rounds
   const int rows_len = master_rows_len(N, nthr, VPT, NEWTON);
   float *s_pp = s_rows + rows_len;                // [N*NG] warp partial per (slot, subtile) pair
-  int *s_i = (int *)(s_pp + N * NG);              // [8]: 1 nonzero slots, 2 nonzero pairs
+  int *s_i = (int *)(s_pp + N * NG);              // [8]: 2 nonzero pairs, 3 free slots (Newton)
   int *s_beam = s_i + 8;                          // [N] beam of slot
-  int *s_nz = s_beam + N;                         // [N] slots with a nonzero subtile here
-  int *s_mask = s_nz + N;                         // [N] per slot: bit m = subtile m nonzero
+  int *s_mask = s_beam + N;                       // [N] per slot: bit m = subtile m nonzero
   int *s_pst = s_mask + N;                        // [N+1] first pair of each slot
   int *s_pair = s_pst + N + 1;                    // [N*NG] pairs s*8+m in slot order
   int *s_mcnt = s_pair + N * NG;                  // [8] nonzero columns of each own subtile
@@ -708,7 +722,6 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
   for (int q = tid; q < 768; q += nthr) s_tab[q] = a.tabf[q];
   if (XP)
     for (int q = tid; q < 768; q += nthr) s_tablo[q] = (float)(a.tabd[q] - (double)a.tabf[q]);
-  for (int q = tid; q < 33 * nthr; q += nthr) s_rows[q] = 0.f;
   for (int k = tid; k < N; k += nthr) {
     s_y[k] = a.y[k];
     s_d[k] = 0.0;
@@ -733,23 +746,41 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
     s_mask[s] = mk;
   }
   __syncthreads();
-  if (tid == 0) {  // nonzero columns and (column, subtile) pairs, in slot order
-    int n = 0, np = 0;
-    for (int s = 0; s < ns; ++s) {
-      const int mk = s_mask[s];
-      s_pst[s] = np;
-      if (mk) s_nz[n++] = s;
-      for (int m = 0; m < NG; ++m)
-        if (mk >> m & 1) s_pair[np++] = s * 8 + m;
+  if (warp == 0) {  // nonzero (column, subtile) pairs and per-subtile column lists, in slot order
+    const unsigned lt = (1u << lane) - 1u;
+    int np = 0, cnt[NG];
+#pragma unroll
+    for (int m = 0; m < NG; ++m) cnt[m] = 0;
+    for (int base = 0; base < ns; base += 32) {
+      const int s = base + lane;
+      const int mk = s < ns ? s_mask[s] : 0;
+      const int pc = __popc(mk);
+      int incl = pc;  // inclusive prefix of the pair counts over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (s < ns) {
+        int p = np + incl - pc;
+        s_pst[s] = p;
+#pragma unroll
+        for (int m = 0; m < NG; ++m)
+          if (mk >> m & 1) s_pair[p++] = s * 8 + m;
+      }
+      np += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+      for (int m = 0; m < NG; ++m) {
+        const unsigned b = __ballot_sync(0xffffffffu, mk >> m & 1);
+        if (mk >> m & 1) s_mcols[m * N + cnt[m] + __popc(b & lt)] = s;
+        cnt[m] += __popc(b);
+      }
     }
-    s_pst[ns] = np;
-    s_i[1] = n;
-    s_i[2] = np;
-    for (int m = 0; m < NG; ++m) {
-      int c = 0;
-      for (int s = 0; s < ns; ++s)
-        if (s_mask[s] >> m & 1) s_mcols[m * N + c++] = s;
-      s_mcnt[m] = c;
+    if (lane == 0) {
+      s_pst[ns] = np;
+      s_i[2] = np;
+#pragma unroll
+      for (int m = 0; m < NG; ++m) s_mcnt[m] = cnt[m];
     }
   }
   __syncthreads();
@@ -758,7 +789,7 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
     s_yf[s] = (float)yk;
     s_ylo[s] = (float)(yk - (double)(float)yk);
   }
-  const int nnzs = s_i[1], npairs = s_i[2];
+  const int npairs = s_i[2];
 
   uint32_t my_sid[NG];
 #pragma unroll
@@ -768,8 +799,12 @@ __global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArg
   __syncthreads();
 
   // the dose excess e = M y - T of the thread's voxels
-  excess_from_y<VPT>(a, z, XP ? zl : nullptr, my_sid, s_tab, XP ? s_tablo : nullptr, s_nz, s_mask,
-                     s_yf, s_ylo, nnzs, SUB_OFF(0), G * ST);
+  excess_from_y<VPT, XP, master_pipe_stages(VPT)>(a, z, XP ? zl : nullptr, my_sid, s_tab,
+                                                   XP ? s_tablo : nullptr, s_mcnt, s_mcols, N, s_yf,
+                                                   s_ylo, (float4 *)s_rows, SUB_OFF(0), G * ST);
+  cp_async_wait<0>();
+  __syncthreads();  // every thread's copies have landed before the rows are cleared
+  for (int q = tid; q < 33 * nthr; q += nthr) s_rows[q] = 0.f;
 
   int it = 0, status = VMAT_ENOTCONV, nsync = 0;
   double rho = 0.0, rho0 = 0.0, tol = 0.0;
@@ -1746,7 +1781,7 @@ static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton, bool xp) 
              (size_t)nthr * vpt * 4 +                          // F' tile
              (size_t)master_rows_len(N, nthr, vpt, newton) * 4 +  // line-search rows, pipeline, Newton
              (size_t)N * ng * 4 +                              // pair partials
-             (size_t)(8 + 4 * N + 1 + N * ng) * 4 +            // i beam nz mask pst pair
+             (size_t)(8 + 3 * N + 1 + N * ng) * 4 +            // i beam mask pst pair
              (size_t)(8 + N * ng) * 4;                          // per-subtile column lists
   if (newton) b += (size_t)(2 * N + 8 + ng * N) * 4 + (size_t)(2 * N + 2 * (N + 1)) * 4;
   if (xp) b += 16 + (size_t)nthr * vpt * 4 + 768 * 4 + (size_t)N * ng * 4;  // alignment, low parts:
