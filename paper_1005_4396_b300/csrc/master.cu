@@ -648,8 +648,11 @@ __device__ __forceinline__ void excess_from_y(const MasterArgs &a, float *z, flo
   }
 }
 
-template <int VPT, bool NEWTON, bool XP>
-__global__ void __launch_bounds__(master_max_threads(VPT), 1) k_master(MasterArgs a) {
+// MAXT: the largest CTA the build serves.  Launches of at most 384 threads
+// take a build bounded to 384 (up to 168 registers a thread, where 512
+// threads allow 128 and the kernel would spill).
+template <int VPT, bool NEWTON, bool XP, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_master(MasterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, ns = a.nslots, tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -1792,21 +1795,29 @@ static size_t master_smem_bytes(int N, int nthr, int vpt, bool newton, bool xp) 
 
 // The master kernel for a launch shape and variant; nullptr where the
 // variant is not built (extended precision stops at 16 voxels per thread).
-static const void *master_fn(int vpt, bool newton, bool xp) {
-#define VMAT_MFN(V)                                                                        \
-  if (vpt == V)                                                                           \
-    return newton ? (xp ? (const void *)k_master<V, true, true> : (const void *)k_master<V, true, false>) \
-                  : (xp ? (const void *)k_master<V, false, true> : (const void *)k_master<V, false, false>);
+// The FP32 gradient projection at 4 or 8 voxels per thread has a build for
+// CTAs of at most 384 threads.
+static const void *master_fn(int vpt, bool newton, bool xp, int nthr) {
+  constexpr int M = master_max_threads(0);
+  if (!newton && !xp && nthr <= 384) {
+    if (vpt == 4) return (const void *)k_master<4, false, false, 384>;
+    if (vpt == 8) return (const void *)k_master<8, false, false, 384>;
+  }
+#define VMAT_MFN(V)                                                                              \
+  if (vpt == V)                                                                                 \
+    return newton ? (xp ? (const void *)k_master<V, true, true, M> : (const void *)k_master<V, true, false, M>) \
+                  : (xp ? (const void *)k_master<V, false, true, M> : (const void *)k_master<V, false, false, M>);
   VMAT_MFN(4)
   VMAT_MFN(8)
   VMAT_MFN(16)
 #undef VMAT_MFN
-  if (vpt == 32 && !xp) return newton ? (const void *)k_master<32, true, false> : (const void *)k_master<32, false, false>;
+  if (vpt == 32 && !xp)
+    return newton ? (const void *)k_master<32, true, false, M> : (const void *)k_master<32, false, false, M>;
   return nullptr;
 }
 
 static cudaError_t master_occupancy_any(int vpt, bool newton, bool xp, int nthr, size_t smem, int *nb) {
-  const void *fn = master_fn(vpt, newton, xp);
+  const void *fn = master_fn(vpt, newton, xp, nthr);
   if (!fn) {
     *nb = 0;
     return cudaSuccess;
@@ -1845,7 +1856,7 @@ vmat_status vmat_configure_master(vmat_ctx *ctx) {
   int64_t chunk = (int64_t)nthr * vpt;
   int grid = (int)((Va + chunk - 1) / chunk);
   const bool xp = ctx->master_xp != 0;
-  if (xp && !master_fn(vpt, false, true))
+  if (xp && !master_fn(vpt, false, true, nthr))
     return vmat_fail(ctx, VMAT_EINVAL,
                      "extended-precision master: at most 16 active voxels per thread (%lld active "
                      "voxels need %d)", (long long)Va, vpt);
@@ -1939,7 +1950,7 @@ vmat_status vmat_launch_master(vmat_ctx *ctx, int max_iters, double kkt_tol, dou
   VMAT_CUDA(ctx, cudaMemsetAsync(ctx->bar, 0, 8, ctx->stream));
   void *args[] = {&a};
   dim3 grid(ctx->master_grid), block(ctx->master_block);
-  const void *fn = master_fn(ctx->master_vpt, pn, ctx->master_xp != 0);
+  const void *fn = master_fn(ctx->master_vpt, pn, ctx->master_xp != 0, ctx->master_block);
   if (!fn) return vmat_fail(ctx, VMAT_EINVAL, "no master kernel for this launch shape and precision");
   const size_t smem = pn ? ctx->master_smem_pn : ctx->master_smem;
   // the dynamic shared-memory limit is a per-kernel, process-wide attribute:
