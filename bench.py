@@ -37,13 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
 # current kernel on the plan's own apertures (bench.py --case master-plan
-# --case-cols 90 --case-ctas 73: 69.286144 MB read + 1.085952 MB written
+# --case-cols 90 --case-ctas 73: 66.889728 MB read + 0.838400 MB written
 # against 3,922,386,944 algorithmic bytes of that launch); set to None
 # whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (69.286144e6 + 1.085952e6) / 3922386944
-# L2 sector peak of that capture: 200,342,828 sectors in 1.547808 ms at
-# 11.895732% of peak sustained elapsed, 32 B per sector
-L2_PEAK_GBS = 200342828 / 1.547808e-3 / 0.11895732 * 32 / 1e9
+MASTER_TRAFFIC_RATIO = (66.889728e6 + 0.8384e6) / 3922386944
+# L2 sector peak of that capture: 201,187,744 sectors in 1.418688 ms at
+# 13.027469% of peak sustained elapsed, 32 B per sector
+L2_PEAK_GBS = 201187744 / 1.418688e-3 / 0.13027469 * 32 / 1e9
 UNIT = "CG iters/s"
 
 
