@@ -1505,7 +1505,58 @@ __global__ void __launch_bounds__(MAXT, 1) k_master(MasterArgs a) {
     // the columns are mostly L2-resident, so latency bounds this pass)
     // the excess e is carried by the updates e += t w; every 16th iteration it
     // is recomputed from y so that FP32 rounding cannot accumulate
-    {
+    if (MAXT <= 384 && !XP) {
+      // (the 384-thread build, with registers to spare) the segments in
+      // batches of BQ plain 16-byte loads per thread, all in flight at once,
+      // then summed in column order: the same sums as the ring below
+      const bool refresh = (it & 15) == 15;
+      constexpr int BQ = 6;  // (4..12 measured on the prostate plan: 6 is the fastest)
+      const size_t vp4 = (size_t)a.Vpad / 4;
+#pragma unroll
+      for (int m = 0; m < NG; ++m) {
+        const int nm = s_mcnt[m];
+        const int *cl = s_mcols + m * N;
+        const float4 *src = (const float4 *)(a.M + SUB_OFF(m)) + tid;
+        float4 ww = make_float4(0.f, 0.f, 0.f, 0.f), zz = ww, zc4 = ww;
+        if (refresh) {
+          zz.x = -s_tab[sid_of(my_sid, 4 * m)];
+          zz.y = -s_tab[sid_of(my_sid, 4 * m + 1)];
+          zz.z = -s_tab[sid_of(my_sid, 4 * m + 2)];
+          zz.w = -s_tab[sid_of(my_sid, 4 * m + 3)];
+        }
+        for (int q0 = 0; q0 < nm; q0 += BQ) {
+          float4 v[BQ];
+#pragma unroll
+          for (int u = 0; u < BQ; ++u)
+            if (q0 + u < nm) v[u] = __ldcg(src + (size_t)cl[q0 + u] * vp4);
+#pragma unroll
+          for (int u = 0; u < BQ; ++u) {
+            if (q0 + u < nm) {
+              const int sl = cl[q0 + u];
+              const float ds = s_df[sl];
+              if (refresh) {
+                const float ys = s_yf[sl], yl = s_ylo[sl];
+                dot2_add(zz.x, zc4.x, v[u].x, ys, yl);
+                dot2_add(zz.y, zc4.y, v[u].y, ys, yl);
+                dot2_add(zz.z, zc4.z, v[u].z, ys, yl);
+                dot2_add(zz.w, zc4.w, v[u].w, ys, yl);
+              }
+              ww.x = fmaf(v[u].x, ds, ww.x);
+              ww.y = fmaf(v[u].y, ds, ww.y);
+              ww.z = fmaf(v[u].z, ds, ww.z);
+              ww.w = fmaf(v[u].w, ds, ww.w);
+            }
+          }
+        }
+        if (refresh) {
+          z[4 * m] = __fadd_rn(zz.x, zc4.x); z[4 * m + 1] = __fadd_rn(zz.y, zc4.y);
+          z[4 * m + 2] = __fadd_rn(zz.z, zc4.z); z[4 * m + 3] = __fadd_rn(zz.w, zc4.w);
+        }
+        w[4 * m] = ww.x; w[4 * m + 1] = ww.y; w[4 * m + 2] = ww.z; w[4 * m + 3] = ww.w;
+      }
+#pragma unroll
+      for (int p = 0; p < 33; ++p) s_rows[tid * 33 + p] = 0.f;
+    } else {
       const bool refresh = (it & 15) == 15;  // (iteration 0 starts from a fresh e; the update
                                               // before a refresh forms y as a float pair)
       constexpr int STG = master_pipe_stages(VPT);
