@@ -37,13 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "CG iters/s & SpMV HBM GB/s (% of peak); FP16-D vs FP32-D at ≤0.5% dose err"
 # DRAM bytes / algorithmic bytes of k_master from one ncu capture of the
 # current kernel on the plan's own apertures (bench.py --case master-plan
-# --case-cols 90 --case-ctas 73: 65.283584 MB read + 0.837376 MB written
+# --case-cols 90 --case-ctas 73: 65.284864 MB read + 0.806656 MB written
 # against 3,922,386,944 algorithmic bytes of that launch); set to None
 # whenever the kernel changes until it has been captured again
-MASTER_TRAFFIC_RATIO = (65.283584e6 + 0.837376e6) / 3922386944
-# L2 sector peak of that capture: 140,848,500 sectors in 1.371424 ms at
-# 9.434355% of peak sustained elapsed, 32 B per sector
-L2_PEAK_GBS = 140848500 / 1.371424e-3 / 0.09434355 * 32 / 1e9
+MASTER_TRAFFIC_RATIO = (65.284864e6 + 0.806656e6) / 3922386944
+# L2 sector peak of that capture: 140,826,227 sectors in 1.361408 ms at
+# 9.510887% of peak sustained elapsed, 32 B per sector
+L2_PEAK_GBS = 140826227 / 1.361408e-3 / 0.09510887 * 32 / 1e9
 UNIT = "CG iters/s"
 
 

@@ -117,7 +117,9 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *dstatus, unsigned 
     const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
     unsigned old, cur;
     int ok = 1;
-    __threadfence();  // the CTA's partials (ordered by the bar.sync above) before arriving
+    // the release is cumulative: the CTA's partials, ordered before this
+    // thread by the bar.sync above, are visible to every CTA that acquires
+    // the flipped word (no separate fence needed)
     asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc)
                  : "memory");
     const unsigned long long t0 = vmat_globaltimer();
